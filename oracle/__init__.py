@@ -1,0 +1,119 @@
+"""ORACLE -- test infrastructure only.
+
+A plain fp64 CPU restatement of the paper's FSR and SSR reconstructions (Sec. III-B,
+Def. 2, Eq. 4), written in C (``oracle.c``) and driven through ctypes, plus a pure-Python
+literal reading of Def. 2 for tiny inputs (``bruteforce.py``).  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import it; the
+library in ``paper_2412_11639_gb300`` never does, and the two share no code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into an in-tree shared library (plain C, OpenMP over pixels)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-ffp-contract=off", _SRC, "-o", tmp])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        c = ctypes
+        lib.oracle_reconstruct.argtypes = [c.c_void_p, c.c_int64, c.c_int64, c.c_int, c.c_double,
+                                           c.c_int, c.c_int, c.c_void_p, c.c_int64, c.c_void_p,
+                                           c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p,
+                                           c.c_void_p, c.c_void_p, c.c_void_p]
+        lib.oracle_reconstruct.restype = c.c_int
+        lib.oracle_spike_times.argtypes = [c.c_void_p, c.c_int64, c.c_int, c.c_int64, c.c_void_p]
+        lib.oracle_spike_times.restype = c.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def spike_times(stream: np.ndarray, T: int, p: int) -> np.ndarray:
+    """Spike times of pixel p (step 1)."""
+    stream = np.ascontiguousarray(stream)
+    out = np.empty(T, dtype=np.int32)
+    K = _load().oracle_spike_times(stream.ctypes.data, stream.shape[1], T, p, out.ctypes.data)
+    return out[:K].copy()
+
+
+class Result:
+    """Oracle output for a set of pixels.
+
+    frames:   fp64 [T_out][npix] (or None)
+    K:        int32 [npix] spike counts
+    nseg:     int32 [npix] stable-sequence counts
+    seg_off:  int64 [npix+1] offsets into the seg_* arrays (when segments were asked for)
+    seg_ts, seg_te, seg_n: int32 start spike time, end spike time, interval count
+    seg_val:  fp64 theta * N / (t_end - t_start)
+    """
+
+    def __init__(self):
+        self.frames = self.K = self.nseg = self.seg_off = None
+        self.seg_ts = self.seg_te = self.seg_n = self.seg_val = None
+
+    def segments(self, i: int):
+        a, b = self.seg_off[i], self.seg_off[i + 1]
+        return (self.seg_ts[a:b], self.seg_te[a:b], self.seg_n[a:b], self.seg_val[a:b])
+
+
+def reconstruct(stream: np.ndarray, H: int, W: int, T: int, theta: float = 1.0, order: int = 1,
+                stride: int = 1, pixels=None, frames: bool = True,
+                segments: bool = False) -> Result:
+    """Run the oracle on packed stream [T][pitch] for the given pixels (default: all)."""
+    stream = np.ascontiguousarray(stream, dtype=np.uint8)
+    if stream.ndim != 2 or stream.shape[0] < T:
+        raise ValueError("stream must be [T][pitch]")
+    P = H * W
+    pitch = stream.shape[1]
+    pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
+    npix = P if pix is None else pix.shape[0]
+    T_out = (T + stride - 1) // stride
+    r = Result()
+    r.K = np.empty(npix, dtype=np.int32)
+    r.nseg = np.empty(npix, dtype=np.int32)
+    lib = _load()
+    fr = np.empty((T_out, npix), dtype=np.float64) if frames else None
+    rc = lib.oracle_reconstruct(stream.ctypes.data, pitch, P, T, theta, order, stride, _ptr(pix),
+                                npix, _ptr(fr), r.K.ctypes.data, r.nseg.ctypes.data,
+                                None, None, None, None, None)
+    if rc != 0:
+        raise ValueError(f"oracle_reconstruct failed ({rc})")
+    r.frames = fr
+    if segments:
+        off = np.zeros(npix + 1, dtype=np.int64)
+        np.cumsum(r.nseg, out=off[1:])
+        tot = int(off[-1])
+        r.seg_off = off
+        r.seg_ts = np.empty(tot, dtype=np.int32)
+        r.seg_te = np.empty(tot, dtype=np.int32)
+        r.seg_n = np.empty(tot, dtype=np.int32)
+        r.seg_val = np.empty(tot, dtype=np.float64)
+        rc = lib.oracle_reconstruct(stream.ctypes.data, pitch, P, T, theta, order, stride,
+                                    _ptr(pix), npix, None, None, None, off.ctypes.data,
+                                    r.seg_ts.ctypes.data, r.seg_te.ctypes.data,
+                                    r.seg_n.ctypes.data, r.seg_val.ctypes.data)
+        if rc != 0:
+            raise ValueError(f"oracle_reconstruct (segments) failed ({rc})")
+    return r

@@ -1,0 +1,217 @@
+/*
+ * ORACLE -- test infrastructure only.  Plain, slow, fp64 CPU restatement of the
+ * paper's two parameter-free reconstructions (FSR and SSR, Sec. III-B) and of the
+ * segment intensity of Eq. 4.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may call it; the product path never does.  It shares no code with
+ * the CUDA path.
+ *
+ * Steps, per pixel, in the paper's order:
+ *   1. spike times s_1 < ... < s_K of the binary stream S_0 (Eq. 2 output);
+ *   2. interval stream S_1 = {T_0(i)}, T_0(i) = s_{i+1} - s_i (Def. 2, Eq. 5);
+ *   3. FSR: break S_1 greedily wherever the next element would violate the
+ *      zero-order rule (Def. 2: one value, or two values differing by 1); the
+ *      violating element opens the next stable sequence (Sec. III-C, Fig. 4 text);
+ *   4. SSR (order 2): inside each FSR sequence with values {a, a+1}, form S_2 for the
+ *      '-' choice (firing value a) and the '+' choice (firing value a+1): the index
+ *      distances between consecutive occurrences of that value in S_1 (Def. 2 applied
+ *      to S_1, Fig. 1).  Break each S_2 greedily by the same zero-order rule; a break
+ *      before distance d_j = q_{j+1} - q_j cuts S_1 after element q_j.  The cuts of
+ *      both choices are united and split the FSR sequence (Sec. III-B);
+ *   5. intensity of a stable sequence of N intervals: theta / ((1/N) sum T_0(i)) (Eq. 4,
+ *      with 255 generalised to the threshold argument theta);
+ *   6. frames: frame k samples t_k = k * stride and takes the value of the sequence
+ *      covering t_k, a sequence of intervals i0..i1 covering the steps
+ *      (s_{i0}, s_{i1+1}].  Steps up to s_1 take the first sequence's value, steps
+ *      after s_K the last one's, and a pixel with fewer than two spikes reads 0.
+ *
+ * Readings where the paper is silent (frame policy, cut position, hierarchy of the
+ * two orders) are the ones listed in the design notes of this repository.
+ *
+ * Time indices are 0-based steps n = 0 .. T-1.  Values are fp64.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* bit of pixel p in frame n of a [T][pitch] LSB-first packed stream */
+static int spike_bit(const uint8_t *stream, int64_t pitch, int n, int64_t p) {
+    return (stream[(int64_t)n * pitch + (p >> 3)] >> (p & 7)) & 1;
+}
+
+/* Step 1: spike times of pixel p; returns K. */
+int oracle_spike_times(const uint8_t *stream, int64_t pitch, int T, int64_t p, int32_t *times) {
+    int K = 0;
+    for (int n = 0; n < T; ++n)
+        if (spike_bit(stream, pitch, n, p)) times[K++] = n;
+    return K;
+}
+
+/* zero-order rule of Def. 2 for a running range [lo, hi] of integers */
+static int zero_order_ok(int lo, int hi) { return hi - lo <= 1; }
+
+/*
+ * Steps 2-5 for one pixel.  s[0..K-1] are spike times.  Writes up to K-1 segments:
+ * t_start[j], t_end[j] (spike times bounding the segment), n_int[j] (number of
+ * intervals N) and val[j] = theta * N / (t_end - t_start).  Returns the count.
+ * work must hold 3 * K ints.
+ */
+int oracle_segments(const int32_t *s, int K, int order, double theta, int32_t *t_start,
+                    int32_t *t_end, int32_t *n_int, double *val, int32_t *work) {
+    if (K < 2) return 0;
+    int n = K - 1;                    /* number of intervals */
+    int32_t *x = work;                /* S_1 */
+    int32_t *cut_after = work + n;    /* 1 if a stable sequence ends at this interval */
+    int32_t *pos = work + 2 * n;      /* positions of one value inside a segment */
+    for (int i = 0; i < n; ++i) {
+        x[i] = s[i + 1] - s[i];
+        cut_after[i] = 0;
+    }
+    cut_after[n - 1] = 1;
+
+    /* Step 3: FSR, greedy zero-order segmentation of S_1. */
+    int lo = x[0], hi = x[0];
+    for (int i = 1; i < n; ++i) {
+        int nlo = x[i] < lo ? x[i] : lo;
+        int nhi = x[i] > hi ? x[i] : hi;
+        if (zero_order_ok(nlo, nhi)) {
+            lo = nlo;
+            hi = nhi;
+        } else {
+            cut_after[i - 1] = 1;     /* the violating element opens the next sequence */
+            lo = hi = x[i];
+        }
+    }
+
+    /* Step 4: SSR, second-order test inside every FSR sequence. */
+    if (order >= 2) {
+        int i0 = 0;
+        while (i0 < n) {
+            int i1 = i0;
+            while (!cut_after[i1]) ++i1;          /* FSR sequence [i0, i1] */
+            int a = x[i0];
+            for (int i = i0; i <= i1; ++i)
+                if (x[i] < a) a = x[i];
+            int fsr_end = i1;
+            for (int v = a; v <= a + 1; ++v) {     /* '-' then '+' */
+                int m = 0;
+                for (int i = i0; i <= fsr_end; ++i)
+                    if (x[i] == v) pos[m++] = i;
+                if (m < 3) continue;              /* fewer than two distances: no break */
+                int dlo = pos[1] - pos[0], dhi = dlo;
+                for (int j = 1; j + 1 < m; ++j) {
+                    int d = pos[j + 1] - pos[j];
+                    int nlo = d < dlo ? d : dlo;
+                    int nhi = d > dhi ? d : dhi;
+                    if (zero_order_ok(nlo, nhi)) {
+                        dlo = nlo;
+                        dhi = nhi;
+                    } else {
+                        cut_after[pos[j]] = 1;   /* d_j spans S_1 elements pos[j]+1 .. pos[j+1] */
+                        dlo = dhi = d;
+                    }
+                }
+            }
+            i0 = fsr_end + 1;
+        }
+    }
+
+    /* Step 5: one value per stable sequence (Eq. 4). */
+    int nseg = 0, i0 = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!cut_after[i]) continue;
+        int N = i - i0 + 1;
+        int ts = s[i0], te = s[i + 1];
+        t_start[nseg] = ts;
+        t_end[nseg] = te;
+        n_int[nseg] = N;
+        double mean_interval = (double)(te - ts) / (double)N;   /* (1/N) sum T_0(i) */
+        val[nseg] = theta / mean_interval;
+        ++nseg;
+        i0 = i + 1;
+    }
+    return nseg;
+}
+
+/* Step 6 for one pixel: frames[k * fstride] for k = 0 .. ceil(T/stride)-1. */
+void oracle_frames(int K, int nseg, const int32_t *t_start, const int32_t *t_end,
+                   const double *val, int T, int stride, double *frames, int64_t fstride) {
+    int T_out = (T + stride - 1) / stride;
+    int j = 0;
+    for (int k = 0; k < T_out; ++k) {
+        int64_t t = (int64_t)k * stride;
+        double v;
+        if (K < 2 || nseg == 0) {
+            v = 0.0;
+        } else if (t <= t_start[0]) {
+            v = val[0];                               /* before the first spike */
+        } else if (t > t_end[nseg - 1]) {
+            v = val[nseg - 1];                        /* after the last spike */
+        } else {
+            while (!(t_start[j] < t && t <= t_end[j])) ++j;   /* covering sequence */
+            v = val[j];
+        }
+        frames[(int64_t)k * fstride] = v;
+    }
+}
+
+/*
+ * Whole-stream driver over a list of pixels (all pixels when pix == NULL), OpenMP over
+ * pixels.  Any output pointer may be NULL.
+ *   frames  [T_out][npix] fp64
+ *   K       [npix] spike counts
+ *   nseg    [npix] segment counts
+ *   seg_off [npix+1] (input): if given together with seg_* buffers, pixel i's segments
+ *           are written at seg_off[i] .. seg_off[i+1]-1; a pixel whose count differs
+ *           from its slot size makes the call return -2.
+ * Returns 0, -1 on bad arguments, -2 on a segment-slot mismatch.
+ */
+int oracle_reconstruct(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta,
+                       int order, int stride, const int64_t *pix, int64_t npix, double *frames,
+                       int32_t *K_out, int32_t *nseg_out, const int64_t *seg_off,
+                       int32_t *seg_ts, int32_t *seg_te, int32_t *seg_n, double *seg_val) {
+    if (P <= 0 || T <= 0 || pitch * 8 < P || stride <= 0 || order < 1 || order > 2) return -1;
+    if (pix == NULL) npix = P;
+    int err = 0;
+#pragma omp parallel
+    {
+        int32_t *s = (int32_t *)malloc(sizeof(int32_t) * (size_t)T);
+        int32_t *ts = (int32_t *)malloc(sizeof(int32_t) * (size_t)T);
+        int32_t *te = (int32_t *)malloc(sizeof(int32_t) * (size_t)T);
+        int32_t *nn = (int32_t *)malloc(sizeof(int32_t) * (size_t)T);
+        double *vv = (double *)malloc(sizeof(double) * (size_t)T);
+        int32_t *work = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)T);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < npix; ++i) {
+            int64_t p = pix ? pix[i] : i;
+            if (p < 0 || p >= P) {
+#pragma omp atomic write
+                err = -1;
+                continue;
+            }
+            int K = oracle_spike_times(stream, pitch, T, p, s);
+            int ns = oracle_segments(s, K, order, theta, ts, te, nn, vv, work);
+            if (K_out) K_out[i] = K;
+            if (nseg_out) nseg_out[i] = ns;
+            if (seg_off && seg_ts) {
+                if (seg_off[i + 1] - seg_off[i] != ns) {
+#pragma omp atomic write
+                    err = -2;
+                } else {
+                    int64_t o = seg_off[i];
+                    memcpy(seg_ts + o, ts, sizeof(int32_t) * (size_t)ns);
+                    memcpy(seg_te + o, te, sizeof(int32_t) * (size_t)ns);
+                    memcpy(seg_n + o, nn, sizeof(int32_t) * (size_t)ns);
+                    memcpy(seg_val + o, vv, sizeof(double) * (size_t)ns);
+                }
+            }
+            if (frames) oracle_frames(K, ns, ts, te, vv, T, stride, frames + i, npix);
+        }
+        free(s);
+        free(ts);
+        free(te);
+        free(nn);
+        free(vv);
+        free(work);
+    }
+    return err;
+}
