@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Throughput of the spike-stream reconstruction (FSR / SSR, arXiv 2412.11639) on GB300.
+
+A step is one reconstruction of the whole workload: the default is the moving-scene
+sensor stream of 250 x 400 pixels x 20000 steps with a frame every 10 steps (fp32),
+SSR (order 2).  Inputs (250 MB) and outputs (800 MB) are both larger than the 129 MB L2,
+so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank reconstructing its own replica
+(weak scaling, no data-path collective); the time is the maximum over ranks.
+--impl reference times the fp64 CPU oracle (the only reference implementation of this
+method here) on the host cores, on a bounded sample of the same workload per step.
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpixel-frames/s at 1 GB300 and % HBM roofline; refiner PSNR gain vs plain"
+UNIT = "Gpixel-frames/s"
+KERNEL = "spk_scan_kernel"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "spk_scan_traffic.txt")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="dynamic_250x400x20000")
+    ap.add_argument("--order", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed ----
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Maximum of a float over all ranks (identity for a single process)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------- clocks ----
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="spk_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self, t0: float, t1: float):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                except ValueError:
+                    continue
+                rows.append((ts, parts))
+            os.unlink(self.path)
+        except OSError:
+            pass
+        inside = [p for ts, p in rows if t0 - 0.05 <= ts <= t1 + 0.05] or [p for _, p in rows]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[2]) for p in inside if num(p[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for p in inside:
+            for name, v in zip(names, p[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(inside[0][3]), "samples": len(inside),
+                "power_w_max": max((num(p[4]) or 0.0) for p in inside),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------- inputs ----
+def workload_stream(name: str, rank: int, world: int):
+    """Generate (rank 0, cached in the temp dir) and load the workload's packed stream."""
+    import numpy as np
+    import spkgen
+    w = spkgen.WORKLOADS[name]
+    cache = os.path.join(tempfile.gettempdir(), f"spk_stream_{name}.npy")
+    if rank == 0 and not os.path.exists(cache):
+        st, _ = spkgen.make_stream(w)
+        tmp = cache + f".{os.getpid()}.tmp.npy"
+        np.save(tmp, st)
+        os.replace(tmp, cache)
+    barrier(world)
+    return w, np.load(cache, mmap_mode=None)
+
+
+def measured_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    cdir = os.path.join(ROOT, "paper_2412_11639_gb300", "csrc")
+    for f in sorted(os.listdir(cdir)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(cdir, f), "rb").read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload: str, order: int):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                kv[k.strip()] = v.strip()
+        if (kv.get("workload") == workload and int(kv.get("order", -1)) == order
+                and kv.get("source_sha256") == kernel_source_sha()):
+            return float(kv["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle ----
+def oracle_rate(st, w, order, pixels=None):
+    """Gpixel-frames/s of the fp64 CPU oracle over the given pixels (all by default)."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.reconstruct(st, w.H, w.W, w.T, 1.0, order, w.stride, pixels=pixels, frames=True)
+    dt = time.perf_counter() - t0
+    npix = w.P if pixels is None else len(pixels)
+    del r
+    return npix * w.T_out / dt / 1e9, dt, npix
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------- arms ----
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    w, st = workload_stream(args.workload, 0, 1)
+    chunk = 1024
+    starts = np.arange(0, w.P, chunk)
+    for i in range(args.warmup):
+        s0 = starts[i % len(starts)]
+        oracle_rate(st, w, args.order, np.arange(s0, min(s0 + chunk, w.P)))
+    t0 = time.perf_counter()
+    units = 0
+    for i in range(args.steps):
+        s0 = starts[i % len(starts)]
+        pix = np.arange(s0, min(s0 + chunk, w.P))
+        oracle_rate(st, w, args.order, pix)
+        units += len(pix) * w.T_out
+    dt = time.perf_counter() - t0
+    value = units / dt / 1e9
+    cores = host_cores()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": config_of(w, args.order),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{chunk} pixels x {w.T_out} frames per step, rotating over the "
+                                   f"{w.P} pixels of {w.name}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w, order):
+    return {"workload": w.name, "H": w.H, "W": w.W, "T": w.T, "frame_stride": w.stride,
+            "T_out": w.T_out, "out_dtype": w.out_dtype, "method": "SSR" if order == 2 else "FSR",
+            "threshold": 1.0, "parallelism": "replicas, one per GPU",
+            "l2": "inputs and outputs larger than the 129 MB L2 (no flush)"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2412_11639_gb300 as pkg
+    from paper_2412_11639_gb300 import spk
+
+    torch.cuda.set_device(local_rank)
+    w, st = workload_stream(args.workload, rank, world)
+    dtype = torch.float16 if w.out_dtype == "f16" else torch.float32
+    esz = 2 if dtype == torch.float16 else 4
+    R = pkg.Reconstructor(order=args.order, stride=w.stride, dtype=dtype, device=local_rank)
+    dev = torch.from_numpy(st).cuda()
+    out = R.alloc_frames(w.H, w.W, w.T)
+    stream = R.stream
+
+    for _ in range(args.warmup):
+        R(dev, w.H, w.W, w.T, 1.0, out=out)
+    R.synchronize()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    n0 = spk.spk_launch_count(R.ctx)
+    t0 = time.time()
+    e0.record(stream)
+    for i in range(K):
+        ev[i][0].record(stream)
+        R(dev, w.H, w.W, w.T, 1.0, out=out)
+        ev[i][1].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier(world)
+    R.synchronize()
+    launches = spk.spk_launch_count(R.ctx) - n0
+    total_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    clk = clocks.stop(t0, t1) if clocks else None
+
+    units = w.P * w.T_out * K * world
+    value = units / (total_ms / 1e3) / 1e9
+    alg_bytes = w.P * w.T / 8 + w.P * w.T_out * esz
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+
+    # end to end through the public C ABI with pinned host buffers (copies timed)
+    e2e = None
+    if args.e2e_steps > 0:
+        h_in = torch.from_numpy(st).pin_memory()
+        h_out = torch.empty((w.T_out, w.H, w.W), dtype=dtype).pin_memory()
+        spk.spk_reconstruct_host(R.ctx, h_in, w.H, w.W, w.T, 1.0, h_out)
+        barrier(world)
+        te0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            spk.spk_reconstruct_host(R.ctx, h_in, w.H, w.W, w.T, 1.0, h_out)
+        te_dt = max_over_ranks(time.perf_counter() - te0, world)
+        e2e = {"value": w.P * w.T_out * args.e2e_steps * world / te_dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(st.nbytes), "d2h_bytes_per_step": int(h_out.numel() * esz)}
+    R.close()
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, dt, npix = oracle_rate(st, w, args.order)
+        cpu = {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": f"the whole workload once ({npix} pixels x {w.T_out} frames, {dt:.1f} s)"}
+    traffic = recorded_traffic(w.name, args.order)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic",
+        "config": config_of(w, args.order),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": KERNEL, "kernel_ms": kern_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo")
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

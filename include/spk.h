@@ -1,0 +1,125 @@
+/*
+ * spk.h -- C ABI of the GB300 spike-camera reconstruction library (libspk.so).
+ *
+ * The library reconstructs intensity frames from the binary stream of a spike camera with
+ * the two parameter-free methods of "High-speed and High-quality Vision Reconstruction of
+ * Spike Camera with Spike Stability Theorem" (Zhang et al., arXiv 2412.11639):
+ *   FSR (first-order stability reconstruction) and SSR (second-order), Sec. III-B.
+ * For every pixel the stream S_0 (Eq. 2 output, one bit per step) gives the interval
+ * stream S_1 (Def. 2, Eq. 5).  S_1 is cut greedily wherever the zero-order rule of Def. 2
+ * (one value, or two values that differ by 1) would break; the breaking element opens the
+ * next stable sequence (Sec. III-C).  SSR also cuts inside each FSR sequence wherever one
+ * of the two second-order streams S_2 ('-': distances between occurrences of the smaller
+ * value, '+': of the larger value, Fig. 1) breaks the same rule; such a break of S_2 cuts
+ * S_1 after the element where the breaking distance starts.  A stable sequence of N
+ * intervals spanning D steps has intensity threshold * N / D (Eq. 4, with the 8-bit scale
+ * 255 generalised to `threshold`).
+ *
+ * Conventions shared by every entry point:
+ *  - Time steps are 0-based, n = 0 .. T-1.  Interval i covers the steps (s_i, s_{i+1}].
+ *  - Stream layout: uint8 [T][pitch], pitch = spk_pitch(H, W) = round_up(ceil(H*W/8), 16).
+ *    Pixel p = y*W + x is bit (p % 8), least significant first, of byte p/8 of its frame.
+ *    Padding bits and bytes are ignored.
+ *  - Frame k (k = 0 .. T_out-1, T_out = spk_num_frames(T, stride)) samples t_k = k*stride
+ *    and holds the value of the stable sequence covering t_k.  Steps up to the first spike
+ *    take the first sequence's value, steps after the last spike the last one's, and a
+ *    pixel with fewer than two spikes reads 0.  Frame layout: [T_out][H][W], row-major.
+ *  - Device pointers must be CUDA device (or managed) memory and 16-byte aligned.
+ *  - Calls are asynchronous on the context's stream unless stated; spk_synchronize()
+ *    waits and reports device-side failures.  A context is not thread-safe: use one per
+ *    host thread.  No C++ exception crosses this boundary.
+ *  - Return codes: SPK_OK (0) or one of the negative SPK_ERR_* codes; spk_last_error()
+ *    then describes the failure.
+ */
+#ifndef SPK_H
+#define SPK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum spk_status {
+    SPK_OK = 0,
+    SPK_ERR_ARG = -1,      /* bad argument: NULL, non-positive size, bad threshold,
+                              misaligned or non-device pointer, size overflow, overlap */
+    SPK_ERR_CUDA = -2,     /* a CUDA runtime or driver call failed */
+    SPK_ERR_OOM = -3,      /* device or host allocation failed */
+    SPK_ERR_TIMEOUT = -4,  /* a bounded device-side wait gave up (reported by spk_synchronize) */
+    SPK_ERR_INTERNAL = -5  /* a device-side consistency check failed */
+};
+
+enum spk_dtype { SPK_F32 = 0, SPK_F16 = 1 };
+
+typedef struct spk_config {
+    int order;          /* 1 = FSR, 2 = SSR */
+    int frame_stride;   /* >= 1: frame k samples step k * frame_stride */
+    int out_dtype;      /* SPK_F32 or SPK_F16 (fp16 is the round-to-nearest-even of the
+                           fp32 value) */
+    int device;         /* CUDA device ordinal */
+    void *stream;       /* cudaStream_t to launch on; NULL = the legacy default stream */
+} spk_config;
+
+typedef struct spk_ctx spk_ctx;
+
+/* Creates a context on cfg->device.  Allocates a small device status word; scratch
+ * buffers are allocated lazily by the calls that need them.  *out receives the handle
+ * (NULL on failure).  Errors: SPK_ERR_ARG (bad cfg), SPK_ERR_CUDA, SPK_ERR_OOM. */
+int spk_create(spk_ctx **out, const spk_config *cfg);
+
+/* Frees every buffer owned by ctx.  NULL is a no-op returning SPK_OK. */
+int spk_destroy(spk_ctx *ctx);
+
+/* Bytes per frame of the stream layout: round_up(ceil(H*W/8), 16); -1 if H or W <= 0. */
+int64_t spk_pitch(int H, int W);
+
+/* Number of frames ceil(T / stride); -1 if T <= 0 or stride <= 0. */
+int64_t spk_num_frames(int T, int stride);
+
+/* Reconstructs every frame of one stream (Sec. III-B, Eq. 4).
+ *   stream      device, uint8 [T][spk_pitch(H, W)], read only, owned by the caller
+ *   H, W, T     sensor rows, columns, steps (> 0)
+ *   threshold   finite, > 0: the scale of Eq. 4 (255 for 8-bit images, 1 for rates)
+ *   out_frames  device, [T_out][H][W] of the context's out_dtype, written completely,
+ *               owned by the caller; must not overlap `stream`
+ * Asynchronous on the context's stream.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA. */
+int spk_reconstruct(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold,
+                    void *out_frames);
+
+/* Same reconstruction with HOST buffers: copies the stream to device buffers owned by the
+ * context (allocated on first use, grown as needed), reconstructs, copies the frames back
+ * and waits.  host_stream: uint8 [T][pitch]; host_frames: [T_out][H][W] of out_dtype.
+ * Page-locked host memory makes the copies asynchronous DMA.  Synchronous.
+ * Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM, SPK_ERR_TIMEOUT, SPK_ERR_INTERNAL. */
+int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W, int T,
+                         float threshold, void *host_frames);
+
+/* Verification export: the stable sequences themselves (the records the paper's FPGA
+ * encoder emits, Sec. III-C).  For pixel p, counts[p] receives the number of sequences;
+ * sequence j < cap is written at index j*H*W + p of t_start (spike time opening it),
+ * t_end (spike time closing it), n_int (number of intervals N) and value
+ * (threshold * N / (t_end - t_start), fp32).  cap may be 0 (counts only; the four
+ * arrays may then be NULL).  All pointers are device memory.  Asynchronous.
+ * Errors: SPK_ERR_ARG, SPK_ERR_CUDA. */
+int spk_segments(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold,
+                 int32_t *counts, int32_t *t_start, int32_t *t_end, int32_t *n_int,
+                 float *value, int cap);
+
+/* Waits for the context's stream, then reads and clears the device status word:
+ * SPK_ERR_TIMEOUT if a bounded device wait gave up, SPK_ERR_INTERNAL if a consistency
+ * check failed, SPK_ERR_CUDA if the stream reported an error, else SPK_OK. */
+int spk_synchronize(spk_ctx *ctx);
+
+/* Human-readable description of the last failure on ctx ("" if none).  Valid until the
+ * next call on ctx.  A NULL ctx returns the message of the last failed spk_create. */
+const char *spk_last_error(const spk_ctx *ctx);
+
+/* Number of kernel launches this context has issued since it was created. */
+int64_t spk_launch_count(const spk_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPK_H */

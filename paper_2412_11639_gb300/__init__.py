@@ -1,0 +1,79 @@
+"""GB300-native spike-camera reconstruction (FSR / SSR of arXiv 2412.11639).
+
+The work happens in libspk.so (CUDA, sm_103a) behind the C ABI of include/spk.h;
+``spk`` is its ctypes binding and ``Reconstructor`` a convenience wrapper that takes
+torch tensors for device memory and streams.
+"""
+from __future__ import annotations
+
+from . import spk
+from .build import build
+from .spk import (SPK_F16, SPK_F32, SpkError, spk_create, spk_destroy, spk_launch_count,
+                  spk_last_error, spk_num_frames, spk_pitch, spk_reconstruct,
+                  spk_reconstruct_host, spk_segments, spk_synchronize)
+
+__all__ = ["spk", "build", "Reconstructor", "SpkError", "SPK_F32", "SPK_F16", "spk_create",
+           "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
+           "spk_reconstruct_host", "spk_segments", "spk_synchronize", "spk_last_error",
+           "spk_launch_count"]
+
+
+class Reconstructor:
+    """One libspk context bound to a torch CUDA stream.
+
+    order 1 = FSR, 2 = SSR; frame k samples step k * stride; dtype torch.float32 or
+    torch.float16.  Device memory comes from torch; the reconstruction runs in libspk.
+    """
+
+    def __init__(self, order: int = 2, stride: int = 1, dtype=None, device: int = 0,
+                 stream=None):
+        import torch
+        self.torch = torch
+        dtype = dtype or torch.float32
+        if dtype not in (torch.float32, torch.float16):
+            raise ValueError("dtype must be torch.float32 or torch.float16")
+        self.dtype = dtype
+        self.order, self.stride, self.device = order, stride, device
+        self.stream = stream or torch.cuda.current_stream(device)
+        self.ctx = spk_create(order, stride, SPK_F16 if dtype == torch.float16 else SPK_F32,
+                              device, self.stream.cuda_stream)
+
+    def close(self):
+        if self.ctx is not None:
+            spk_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_frames(self, H: int, W: int, T: int):
+        return self.torch.empty((spk_num_frames(T, self.stride), H, W), dtype=self.dtype,
+                                device=f"cuda:{self.device}")
+
+    def __call__(self, stream, H: int, W: int, T: int, threshold: float = 1.0, out=None):
+        """Reconstruct frames [T_out][H][W] from a device uint8 stream [T][pitch]."""
+        if out is None:
+            out = self.alloc_frames(H, W, T)
+        spk_reconstruct(self.ctx, stream, H, W, T, threshold, out)
+        return out
+
+    def segments(self, stream, H: int, W: int, T: int, threshold: float = 1.0, cap=None):
+        """Stable sequences per pixel: (counts [P], t_start, t_end, n, value [cap][P])."""
+        torch = self.torch
+        P = H * W
+        dev = f"cuda:{self.device}"
+        counts = torch.empty(P, dtype=torch.int32, device=dev)
+        if cap is None:
+            spk_segments(self.ctx, stream, H, W, T, threshold, counts, None, None, None, None, 0)
+            self.synchronize()
+            cap = int(counts.max().item()) if P else 0
+        arrs = [torch.empty((max(cap, 1), P), dtype=d, device=dev)
+                for d in (torch.int32, torch.int32, torch.int32, torch.float32)]
+        spk_segments(self.ctx, stream, H, W, T, threshold, counts, *arrs, cap)
+        return (counts, *arrs)
+
+    def synchronize(self):
+        spk_synchronize(self.ctx)

@@ -1,0 +1,643 @@
+// libspk: GB300 (sm_103a) spike-camera reconstruction -- kernels and the C ABI of spk.h.
+//
+// One kernel does the whole hot path of Sec. III-B for a block of 256 consecutive pixels:
+//   1. TMA (cp.async.bulk.tensor) stages [64 steps] x [32 bytes] tiles of the bit-packed
+//      stream into shared memory through a 4-stage mbarrier pipeline fed by one producer
+//      warp (the paper's FPGA sequence buffer, Sec. III-C, does the same transposition of
+//      frame-major bits into per-pixel time sequences);
+//   2. each compute warp turns its 32 x 32 bit tile (32 steps x 32 pixels) into one
+//      32-step time word per lane with a 5-stage shuffle transpose;
+//   3. each lane runs the FSR / SSR stability scan (spk_scan.cuh) over the spikes of its
+//      time word (ffs per spike) and receives final stable sequences in time order;
+//   4. a sequence whose span covers new frame samples becomes a record
+//      (last frame index, value = threshold * N / D, Eq. 4) in a per-lane shared-memory
+//      queue -- the analogue of the FPGA encoder's (duration, intensity) records;
+//   5. after every 32 steps the warp writes the frame rows every lane has resolved, one
+//      coalesced row (32 consecutive pixels) per store; a lane whose queue runs full
+//      writes its oldest record on its own.
+// Values are known only when a sequence closes, which may be thousands of steps later
+// (a static pixel is one sequence), so rows are written when resolved, not when sampled.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/spk.h"
+#include "spk_scan.cuh"
+
+namespace {
+
+constexpr int NCW = 8;                   // compute warps per block
+constexpr int BLOCK_PIX = NCW * 32;      // pixels per block
+constexpr int ROW_BYTES = BLOCK_PIX / 8; // bytes of one frame row per block (TMA box x)
+constexpr int TT = 64;                   // steps per TMA tile (box y)
+constexpr int NS = 4;                    // pipeline stages
+constexpr int QCAP = 32;                 // records per lane
+constexpr int NTHREADS = (NCW + 1) * 32; // + one producer warp
+constexpr unsigned FULL = 0xffffffffu;
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bounded waits
+
+// device status bits
+constexpr int DEV_TIMEOUT = 1;
+constexpr int DEV_INTERNAL = 2;
+
+struct Smem {
+    uint8_t stage[NS][TT][ROW_BYTES];
+    unsigned long long full[NS];
+    unsigned long long empty[NS];
+    int rec_k[NCW][QCAP][32];
+    float rec_v[NCW][QCAP][32];
+};
+constexpr size_t SMEM_BYTES = sizeof(Smem) + 128;  // + alignment slack for the TMA tiles
+
+struct Params {
+    int64_t P;      // pixels
+    int T;          // steps
+    int ntiles;     // ceil(T / TT)
+    int stride;     // frame stride
+    int T_out;      // frames
+    float theta;    // threshold of Eq. 4
+    void *out;      // frames [T_out][P]
+    int32_t *counts, *seg_ts, *seg_te, *seg_n;  // segments mode
+    float *seg_v;
+    int cap;
+    int *status;
+};
+
+// ------------------------------------------------------------------ PTX helpers ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// generic-proxy shared loads, ordered before a later async-proxy (TMA) refill of the stage
+__device__ __forceinline__ uint32_t lds_u32(const void *p) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false (and the status word flagged) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_CYCLES) {
+            atomicOr(status, DEV_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map,
+                                            unsigned long long *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// 32 x 32 bit transpose across a warp: lane l holds row l (bit b = element [l][b]);
+// afterwards lane l holds column l (bit t = element [t][l]).  Five block swaps.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1) {
+        const uint32_t m = j == 16 ? 0x0000FFFFu
+                         : j == 8  ? 0x00FF00FFu
+                         : j == 4  ? 0x0F0F0F0Fu
+                         : j == 2  ? 0x33333333u
+                                   : 0x55555555u;
+        uint32_t y = __shfl_xor_sync(FULL, x, j);
+        x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+template <typename OutT> __device__ __forceinline__ OutT to_out(float v);
+template <> __device__ __forceinline__ float to_out<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_out<__half>(float v) { return __float2half_rn(v); }
+
+// Eq. 4 with the scale generalised: theta / (D / N) = theta * N / D, correctly rounded
+// (theta * N is exact for theta = 1 and N < 2^24).
+__device__ __forceinline__ float seq_value(float theta, int n, int d) {
+    return __fdiv_rn(__fmul_rn(theta, static_cast<float>(n)), static_cast<float>(d));
+}
+
+// --------------------------------------------------------------------- sinks ----
+// Frame records of one lane: (last frame index covered, value) in a per-lane queue.
+template <typename OutT>
+struct FrameSink {
+    int *rk;       // &rec_k[warp][0][lane], slot stride 32
+    float *rv;
+    OutT *col;     // out + p: frame k at col[k * P]
+    int64_t P;
+    float theta;
+    int stride;
+    int head, tail;  // queue positions (monotone)
+    int F;           // frames < F are covered by pushed records
+    int W;           // frames < W are written
+    float last_v;
+
+    __device__ __forceinline__ void store(int k, float v) { col[static_cast<int64_t>(k) * P] = to_out<OutT>(v); }
+
+    __device__ __forceinline__ void drain_one() {  // queue full: write the oldest record alone
+        const int s = (head % QCAP) * 32;
+        const int kl = rk[s];
+        const float v = rv[s];
+        for (int k = W; k <= kl; ++k) store(k, v);
+        if (kl + 1 > W) W = kl + 1;
+        ++head;
+    }
+    __device__ __forceinline__ void push(int kl, float v) {
+        if (tail - head == QCAP) drain_one();
+        const int s = (tail % QCAP) * 32;
+        rk[s] = kl;
+        rv[s] = v;
+        ++tail;
+        F = kl + 1;
+    }
+    __device__ __forceinline__ void operator()(int ts, int te, int n) {
+        const float v = seq_value(theta, n, te - ts);
+        last_v = v;
+        const int kl = te / stride;  // frames with t_k <= te
+        if (kl >= F) push(kl, v);
+    }
+};
+
+struct SegSink {
+    int32_t *ts, *te, *n;
+    float *v;
+    int64_t P, p;
+    float theta;
+    int cap, cnt;
+    __device__ __forceinline__ void operator()(int a, int b, int c) {
+        if (cnt < cap) {
+            const int64_t i = static_cast<int64_t>(cnt) * P + p;
+            ts[i] = a;
+            te[i] = b;
+            n[i] = c;
+            v[i] = seq_value(theta, c, b - a);
+        }
+        ++cnt;
+    }
+};
+
+// Warp-wide write of resolved frame rows.  Normal: rows below the warp minimum of F (full
+// rows).  Forced (a queue is nearly full, or the stream ended): every lane up to its own F.
+template <typename OutT>
+__device__ __forceinline__ void flush_rows(FrameSink<OutT> &sk, bool valid, bool final_flush) {
+    const int Fl = valid ? sk.F : INT_MAX;
+    const int Wl = valid ? sk.W : INT_MAX;
+    const int used = valid ? sk.tail - sk.head : 0;
+    const int Fmin = __reduce_min_sync(FULL, Fl);
+    const int Wmin = __reduce_min_sync(FULL, Wl);
+    const bool forced = final_flush || __reduce_max_sync(FULL, used) > QCAP - 8;
+    int khi, lim;
+    if (forced) {
+        khi = __reduce_max_sync(FULL, valid ? sk.F : 0);
+        lim = sk.F;
+    } else {
+        khi = Fmin;
+        lim = Fmin;
+    }
+    if (Wmin >= khi) return;  // nothing to write (warp-uniform)
+    int ck = INT_MAX;
+    float cv = 0.f;
+    if (valid && sk.head < sk.tail) {
+        const int s = (sk.head % QCAP) * 32;
+        ck = sk.rk[s];
+        cv = sk.rv[s];
+    }
+    for (int k = Wmin; k < khi; ++k) {
+        if (valid && k >= sk.W && k < lim) {
+            if (k > ck) {  // next record (each covers at least one frame)
+                ++sk.head;
+                const int s = (sk.head % QCAP) * 32;
+                ck = sk.rk[s];
+                cv = sk.rv[s];
+            }
+            sk.store(k, cv);
+        }
+    }
+    if (valid && lim > sk.W) {
+        sk.W = lim;
+        if (sk.head < sk.tail && ck < sk.W) ++sk.head;  // head record fully written
+    }
+}
+
+// ------------------------------------------------------------------- the kernel ----
+template <int ORDER, typename OutT, bool SEGMENTS>
+__global__ void __launch_bounds__(NTHREADS, 3)
+    spk_scan_kernel(const __grid_constant__ CUtensorMap tmap, const Params prm) {
+    extern __shared__ uint8_t smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NCW * 32);  // every consumer lane releases
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == NCW) {  // ---------------------------------------- producer warp ----
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+            int issued = 0;
+            for (int j = 0; j < prm.ntiles; ++j) {
+                const int s = j % NS;
+                if (j >= NS && !mbar_wait(&sm.empty[s], ((j / NS) - 1) & 1, prm.status)) break;
+                mbar_arrive_expect_tx(&sm.full[s], TT * ROW_BYTES);
+                tma_load_2d(&sm.stage[s][0][0], &tmap, &sm.full[s], blockIdx.x * ROW_BYTES, j * TT);
+                issued = j + 1;
+            }
+            // let every copy land before this warp leaves (matters only after an error)
+            for (int j = issued > NS ? issued - NS : 0; j < issued; ++j)
+                if (!mbar_wait(&sm.full[j % NS], (j / NS) & 1, prm.status)) break;
+        }
+        return;
+    }
+
+    // ------------------------------------------------------------- compute warps ----
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * BLOCK_PIX + warp * 32 + lane;
+    const bool valid = p < prm.P;
+    spk::PixelScan<ORDER> sc;
+    sc.init();
+
+    FrameSink<OutT> fs;
+    SegSink ss;
+    if constexpr (SEGMENTS) {
+        ss = SegSink{prm.seg_ts, prm.seg_te, prm.seg_n, prm.seg_v, prm.P, p, prm.theta, prm.cap, 0};
+    } else {
+        fs.rk = &sm.rec_k[warp][0][lane];
+        fs.rv = &sm.rec_v[warp][0][lane];
+        fs.col = static_cast<OutT *>(prm.out) + (valid ? p : 0);
+        fs.P = prm.P;
+        fs.theta = prm.theta;
+        fs.stride = prm.stride;
+        fs.head = fs.tail = fs.F = fs.W = 0;
+        fs.last_v = 0.f;
+    }
+
+    bool ok = true;
+    for (int j = 0; j < prm.ntiles; ++j) {
+        const int s = j % NS;
+        // warp-uniform outcome: every lane leaves together if any lane's wait gave up
+        if (!__all_sync(FULL, mbar_wait(&sm.full[s], (j / NS) & 1, prm.status))) {
+            ok = false;
+            break;
+        }
+        const uint32_t r0 = lds_u32(&sm.stage[s][lane][warp * 4]);
+        const uint32_t r1 = lds_u32(&sm.stage[s][lane + 32][warp * 4]);
+        // each lane orders its own reads before the producer may refill this stage
+        fence_proxy_async_smem();
+        mbar_arrive(&sm.empty[s]);
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            uint32_t w = warp_transpose32(h ? r1 : r0, lane);
+            if (!valid) w = 0;
+            const int base = j * TT + h * 32;
+            if (sc.last_t < 0 && w) {  // the stream's first spike opens the first sequence
+                sc.first_spike(base + __ffs(w) - 1);
+                w &= w - 1;
+            }
+            while (w) {
+                const int b = __ffs(w) - 1;
+                w &= w - 1;
+                if constexpr (SEGMENTS) sc.spike(base + b, ss);
+                else sc.spike(base + b, fs);
+            }
+            if constexpr (!SEGMENTS) flush_rows(fs, valid, false);
+        }
+    }
+    if (!ok) return;
+
+    if constexpr (SEGMENTS) {
+        sc.finish(ss);
+        if (valid) prm.counts[p] = ss.cnt;
+    } else {
+        sc.finish(fs);
+        if (valid && fs.F < prm.T_out) fs.push(prm.T_out - 1, fs.last_v);  // tail hold
+        flush_rows(fs, valid, true);
+    }
+    if (valid && sc.err) atomicOr(prm.status, DEV_INTERNAL);
+}
+
+}  // namespace
+
+// ========================================================================= host ====
+struct spk_ctx {
+    spk_config cfg;
+    cudaStream_t stream;
+    int *d_status;
+    uint8_t *d_in;   // spk_reconstruct_host buffers
+    size_t in_cap;
+    void *d_out;
+    size_t out_cap;
+    int64_t launches;
+    char msg[512];
+};
+
+namespace {
+
+thread_local char g_create_msg[512];
+
+int fail(spk_ctx *ctx, int code, const char *fmt, ...) {
+    char *buf = ctx ? ctx->msg : g_create_msg;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int64_t pitch_of(int H, int W) {
+    if (H <= 0 || W <= 0) return -1;
+    int64_t P = static_cast<int64_t>(H) * W;
+    return ((P + 7) / 8 + 15) / 16 * 16;
+}
+
+// common argument checks of the stream-consuming calls
+int check_stream_args(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold) {
+    if (!ctx) return SPK_ERR_ARG;
+    if (!stream) return fail(ctx, SPK_ERR_ARG, "stream is NULL");
+    if (H <= 0 || W <= 0 || T <= 0) return fail(ctx, SPK_ERR_ARG, "H, W, T must be > 0 (got %d, %d, %d)", H, W, T);
+    if (static_cast<int64_t>(H) * W > (1LL << 31) - BLOCK_PIX)
+        return fail(ctx, SPK_ERR_ARG, "H*W too large");
+    if (!std::isfinite(threshold) || !(threshold > 0.f))
+        return fail(ctx, SPK_ERR_ARG, "threshold must be finite and > 0");
+    if (reinterpret_cast<uintptr_t>(stream) % 16) return fail(ctx, SPK_ERR_ARG, "stream is not 16-byte aligned");
+    if (T > (1 << 30)) return fail(ctx, SPK_ERR_ARG, "T too large");
+    return SPK_OK;
+}
+
+int make_tmap(spk_ctx *ctx, CUtensorMap *map, const uint8_t *stream, int64_t pitch, int T) {
+    auto enc = get_encode();
+    if (!enc) return fail(ctx, SPK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(pitch), static_cast<cuuint64_t>(T)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch)};
+    cuuint32_t box[2] = {ROW_BYTES, TT};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(stream), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, SPK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+    return SPK_OK;
+}
+
+template <int ORDER, typename OutT, bool SEG>
+int launch(spk_ctx *ctx, const CUtensorMap &map, const Params &prm) {
+    auto kern = spk_scan_kernel<ORDER, OutT, SEG>;
+    static bool attr_done = false;  // per instantiation
+    if (!attr_done) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
+            return fail(ctx, SPK_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(cudaGetLastError()));
+        attr_done = true;
+    }
+    const int64_t nblk = (prm.P + BLOCK_PIX - 1) / BLOCK_PIX;
+    kern<<<static_cast<unsigned>(nblk), NTHREADS, SMEM_BYTES, ctx->stream>>>(map, prm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    ++ctx->launches;
+    return SPK_OK;
+}
+
+int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold, void *out,
+             int32_t *counts, int32_t *ts, int32_t *te, int32_t *n, float *v, int cap, bool segments) {
+    const int64_t P = static_cast<int64_t>(H) * W;
+    const int64_t pitch = pitch_of(H, W);
+    CUtensorMap map;
+    int rc = make_tmap(ctx, &map, stream, pitch, T);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
+    Params prm{};
+    prm.P = P;
+    prm.T = T;
+    prm.ntiles = (T + TT - 1) / TT;
+    prm.stride = ctx->cfg.frame_stride;
+    prm.T_out = static_cast<int>((static_cast<int64_t>(T) + prm.stride - 1) / prm.stride);
+    prm.theta = threshold;
+    prm.out = out;
+    prm.counts = counts;
+    prm.seg_ts = ts;
+    prm.seg_te = te;
+    prm.seg_n = n;
+    prm.seg_v = v;
+    prm.cap = cap;
+    prm.status = ctx->d_status;
+    const int order = ctx->cfg.order;
+    if (segments) return order == 1 ? launch<1, float, true>(ctx, map, prm) : launch<2, float, true>(ctx, map, prm);
+    if (ctx->cfg.out_dtype == SPK_F16)
+        return order == 1 ? launch<1, __half, false>(ctx, map, prm) : launch<2, __half, false>(ctx, map, prm);
+    return order == 1 ? launch<1, float, false>(ctx, map, prm) : launch<2, float, false>(ctx, map, prm);
+}
+
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+    auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t spk_pitch(int H, int W) { return pitch_of(H, W); }
+
+int64_t spk_num_frames(int T, int stride) {
+    if (T <= 0 || stride <= 0) return -1;
+    return (static_cast<int64_t>(T) + stride - 1) / stride;
+}
+
+int spk_create(spk_ctx **out, const spk_config *cfg) {
+    if (!out) return fail(nullptr, SPK_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, SPK_ERR_ARG, "cfg is NULL");
+    if (cfg->order != 1 && cfg->order != 2) return fail(nullptr, SPK_ERR_ARG, "order must be 1 or 2");
+    if (cfg->frame_stride < 1) return fail(nullptr, SPK_ERR_ARG, "frame_stride must be >= 1");
+    if (cfg->out_dtype != SPK_F32 && cfg->out_dtype != SPK_F16) return fail(nullptr, SPK_ERR_ARG, "bad out_dtype");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, SPK_ERR_CUDA, "no CUDA device");
+    }
+    if (cfg->device < 0 || cfg->device >= ndev) return fail(nullptr, SPK_ERR_ARG, "bad device ordinal");
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return fail(nullptr, SPK_ERR_CUDA, "cudaSetDevice failed");
+    spk_ctx *c = new (std::nothrow) spk_ctx();
+    if (!c) return fail(nullptr, SPK_ERR_OOM, "host allocation failed");
+    c->cfg = *cfg;
+    c->stream = static_cast<cudaStream_t>(cfg->stream);
+    if (cudaMalloc(&c->d_status, 16) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(nullptr, SPK_ERR_OOM, "cudaMalloc of the status word failed");
+    }
+    if (cudaMemset(c->d_status, 0, 16) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return fail(nullptr, SPK_ERR_CUDA, "cudaMemset failed");
+    }
+    *out = c;
+    return SPK_OK;
+}
+
+int spk_destroy(spk_ctx *ctx) {
+    if (!ctx) return SPK_OK;
+    cudaSetDevice(ctx->cfg.device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_status);
+    if (ctx->d_in) cudaFree(ctx->d_in);
+    if (ctx->d_out) cudaFree(ctx->d_out);
+    delete ctx;
+    return SPK_OK;
+}
+
+const char *spk_last_error(const spk_ctx *ctx) { return ctx ? ctx->msg : g_create_msg; }
+
+int64_t spk_launch_count(const spk_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int spk_reconstruct(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold, void *out_frames) {
+    int rc = check_stream_args(ctx, stream, H, W, T, threshold);
+    if (rc) return rc;
+    ctx->msg[0] = 0;
+    if (!out_frames) return fail(ctx, SPK_ERR_ARG, "out_frames is NULL");
+    if (reinterpret_cast<uintptr_t>(out_frames) % 16) return fail(ctx, SPK_ERR_ARG, "out_frames is not 16-byte aligned");
+    const int64_t P = static_cast<int64_t>(H) * W;
+    const int64_t T_out = spk_num_frames(T, ctx->cfg.frame_stride);
+    const size_t esz = ctx->cfg.out_dtype == SPK_F16 ? 2 : 4;
+    const size_t out_bytes = static_cast<size_t>(T_out) * static_cast<size_t>(P) * esz;
+    const size_t in_bytes = static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W));
+    if (overlaps(stream, in_bytes, out_frames, out_bytes)) return fail(ctx, SPK_ERR_ARG, "out_frames overlaps stream");
+    if (!is_device_ptr(stream) || !is_device_ptr(out_frames))
+        return fail(ctx, SPK_ERR_ARG, "stream and out_frames must be device memory");
+    return run_scan(ctx, stream, H, W, T, threshold, out_frames, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                    false);
+}
+
+int spk_segments(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold, int32_t *counts,
+                 int32_t *t_start, int32_t *t_end, int32_t *n_int, float *value, int cap) {
+    int rc = check_stream_args(ctx, stream, H, W, T, threshold);
+    if (rc) return rc;
+    ctx->msg[0] = 0;
+    if (!counts || cap < 0) return fail(ctx, SPK_ERR_ARG, "counts is NULL or cap < 0");
+    if (cap > 0 && (!t_start || !t_end || !n_int || !value)) return fail(ctx, SPK_ERR_ARG, "segment arrays are NULL");
+    if (!is_device_ptr(stream) || !is_device_ptr(counts)) return fail(ctx, SPK_ERR_ARG, "pointers must be device memory");
+    if (cap > 0 && (!is_device_ptr(t_start) || !is_device_ptr(t_end) || !is_device_ptr(n_int) || !is_device_ptr(value)))
+        return fail(ctx, SPK_ERR_ARG, "pointers must be device memory");
+    return run_scan(ctx, stream, H, W, T, threshold, nullptr, counts, t_start, t_end, n_int, value, cap, true);
+}
+
+int spk_synchronize(spk_ctx *ctx) {
+    if (!ctx) return SPK_ERR_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    int st = 0;
+    if (cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "status read failed");
+    if (st) {
+        cudaMemset(ctx->d_status, 0, sizeof(int));
+        if (st & DEV_TIMEOUT) return fail(ctx, SPK_ERR_TIMEOUT, "a bounded device wait gave up");
+        return fail(ctx, SPK_ERR_INTERNAL, "device consistency check failed (status %d)", st);
+    }
+    return SPK_OK;
+}
+
+int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W, int T, float threshold,
+                         void *host_frames) {
+    int rc = check_stream_args(ctx, host_stream, H, W, T, threshold);
+    if (rc) return rc;
+    ctx->msg[0] = 0;
+    if (!host_frames) return fail(ctx, SPK_ERR_ARG, "host_frames is NULL");
+    const int64_t P = static_cast<int64_t>(H) * W;
+    const int64_t T_out = spk_num_frames(T, ctx->cfg.frame_stride);
+    const size_t esz = ctx->cfg.out_dtype == SPK_F16 ? 2 : 4;
+    const size_t out_bytes = static_cast<size_t>(T_out) * static_cast<size_t>(P) * esz;
+    const size_t in_bytes = static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W));
+    cudaSetDevice(ctx->cfg.device);
+    if (in_bytes > ctx->in_cap) {
+        if (ctx->d_in) cudaFree(ctx->d_in);
+        ctx->d_in = nullptr;
+        ctx->in_cap = 0;
+        if (cudaMalloc(&ctx->d_in, in_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) failed", in_bytes);
+        }
+        ctx->in_cap = in_bytes;
+    }
+    if (out_bytes > ctx->out_cap) {
+        if (ctx->d_out) cudaFree(ctx->d_out);
+        ctx->d_out = nullptr;
+        ctx->out_cap = 0;
+        if (cudaMalloc(&ctx->d_out, out_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) failed", out_bytes);
+        }
+        ctx->out_cap = out_bytes;
+    }
+    if (cudaMemcpyAsync(ctx->d_in, host_stream, in_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "H2D copy: %s", cudaGetErrorString(cudaGetLastError()));
+    rc = run_scan(ctx, ctx->d_in, H, W, T, threshold, ctx->d_out, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                  false);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(host_frames, ctx->d_out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "D2H copy: %s", cudaGetErrorString(cudaGetLastError()));
+    return spk_synchronize(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+"""Thin ctypes binding of libspk.so (include/spk.h): argument marshalling only.
+
+Every entry point keeps its C name.  Device buffers may be given as torch tensors or
+raw integer addresses; every step of the reconstruction runs in the CUDA kernels of
+libspk.so.  There is no CPU fallback: if the library is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB
+
+SPK_OK, SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM, SPK_ERR_TIMEOUT, SPK_ERR_INTERNAL = 0, -1, -2, -3, -4, -5
+SPK_F32, SPK_F16 = 0, 1
+
+_c = ctypes
+EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
+           "spk_reconstruct_host", "spk_segments", "spk_synchronize", "spk_last_error",
+           "spk_launch_count")
+
+
+class SpkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class spk_config(ctypes.Structure):
+    _fields_ = [("order", _c.c_int), ("frame_stride", _c.c_int), ("out_dtype", _c.c_int),
+                ("device", _c.c_int), ("stream", _c.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libspk.so (built by build.build()); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libspk.so not found at {path}: run paper_2412_11639_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f32 = _c.c_void_p, _c.c_int, _c.c_int64, _c.c_float
+    lib.spk_create.argtypes = [_c.POINTER(vp), _c.POINTER(spk_config)]
+    lib.spk_create.restype = i32
+    lib.spk_destroy.argtypes = [vp]
+    lib.spk_destroy.restype = i32
+    lib.spk_pitch.argtypes = [i32, i32]
+    lib.spk_pitch.restype = i64
+    lib.spk_num_frames.argtypes = [i32, i32]
+    lib.spk_num_frames.restype = i64
+    lib.spk_reconstruct.argtypes = [vp, vp, i32, i32, i32, f32, vp]
+    lib.spk_reconstruct.restype = i32
+    lib.spk_reconstruct_host.argtypes = [vp, vp, i32, i32, i32, f32, vp]
+    lib.spk_reconstruct_host.restype = i32
+    lib.spk_segments.argtypes = [vp, vp, i32, i32, i32, f32, vp, vp, vp, vp, vp, i32]
+    lib.spk_segments.restype = i32
+    lib.spk_synchronize.argtypes = [vp]
+    lib.spk_synchronize.restype = i32
+    lib.spk_last_error.argtypes = [vp]
+    lib.spk_last_error.restype = _c.c_char_p
+    lib.spk_launch_count.argtypes = [vp]
+    lib.spk_launch_count.restype = i64
+    _lib = lib
+    return lib
+
+
+def _addr(x):
+    """Device/host address of a tensor, a numpy array, or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _check(ctx, rc):
+    if rc != SPK_OK:
+        msg = load().spk_last_error(ctx)
+        raise SpkError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def spk_create(order: int = 2, frame_stride: int = 1, out_dtype: int = SPK_F32, device: int = 0,
+               stream: int | None = None):
+    lib = load()
+    cfg = spk_config(order, frame_stride, out_dtype, device, stream)
+    ctx = _c.c_void_p()
+    rc = lib.spk_create(_c.byref(ctx), _c.byref(cfg))
+    _check(None, rc)
+    return ctx
+
+
+def spk_destroy(ctx):
+    return load().spk_destroy(ctx)
+
+
+def spk_pitch(H: int, W: int) -> int:
+    return load().spk_pitch(H, W)
+
+
+def spk_num_frames(T: int, stride: int) -> int:
+    return load().spk_num_frames(T, stride)
+
+
+def spk_reconstruct(ctx, stream, H, W, T, threshold, out_frames):
+    return _check(ctx, load().spk_reconstruct(ctx, _addr(stream), H, W, T, threshold, _addr(out_frames)))
+
+
+def spk_reconstruct_host(ctx, host_stream, H, W, T, threshold, host_frames):
+    return _check(ctx, load().spk_reconstruct_host(ctx, _addr(host_stream), H, W, T, threshold,
+                                                   _addr(host_frames)))
+
+
+def spk_segments(ctx, stream, H, W, T, threshold, counts, t_start, t_end, n_int, value, cap):
+    return _check(ctx, load().spk_segments(ctx, _addr(stream), H, W, T, threshold, _addr(counts),
+                                           _addr(t_start), _addr(t_end), _addr(n_int), _addr(value),
+                                           cap))
+
+
+def spk_synchronize(ctx):
+    return _check(ctx, load().spk_synchronize(ctx))
+
+
+def spk_last_error(ctx) -> str:
+    m = load().spk_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def spk_launch_count(ctx) -> int:
+    return load().spk_launch_count(ctx)

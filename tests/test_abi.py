@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads and exports every symbol include/spk.h declares; host-side
+argument checks reject bad calls before any device work.  CPU only (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+import paper_2412_11639_gb300 as pkg
+from paper_2412_11639_gb300 import spk
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "spk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(spk_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg.build()
+    return spk.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n          # ctypes resolves exported symbols only
+    assert set(names) == set(spk.EXPORTS)
+
+
+def test_layout_helpers(lib):
+    assert spk.spk_pitch(250, 400) == 12512          # ceil(100000/8)=12500 -> 12512
+    assert spk.spk_pitch(1000, 1000) == 125008
+    assert spk.spk_pitch(1, 1) == 16
+    assert spk.spk_pitch(1, 128) == 16
+    assert spk.spk_pitch(1, 129) == 32
+    assert spk.spk_pitch(0, 5) == -1 and spk.spk_pitch(5, -1) == -1
+    assert spk.spk_num_frames(20000, 10) == 2000
+    assert spk.spk_num_frames(2001, 10) == 201
+    assert spk.spk_num_frames(1, 7) == 1
+    assert spk.spk_num_frames(0, 1) == -1 and spk.spk_num_frames(5, 0) == -1
+
+
+def test_create_rejects_bad_config(lib):
+    out = ctypes.c_void_p()
+    assert lib.spk_create(ctypes.byref(out), None) == spk.SPK_ERR_ARG
+    for cfg in (spk.spk_config(3, 1, 0, 0, None), spk.spk_config(2, 0, 0, 0, None),
+                spk.spk_config(1, 1, 7, 0, None)):
+        assert lib.spk_create(ctypes.byref(out), ctypes.byref(cfg)) == spk.SPK_ERR_ARG
+        assert out.value is None
+        assert spk.spk_last_error(None)
+
+
+def test_null_context_calls(lib):
+    assert lib.spk_destroy(None) == spk.SPK_OK
+    assert lib.spk_reconstruct(None, None, 1, 1, 1, 1.0, None) == spk.SPK_ERR_ARG
+    assert lib.spk_segments(None, None, 1, 1, 1, 1.0, None, None, None, None, None, 0) == spk.SPK_ERR_ARG
+    assert lib.spk_synchronize(None) == spk.SPK_ERR_ARG
+    assert lib.spk_launch_count(None) == 0
+
+
+def test_no_gpu_is_reported_not_faked(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(spk.SpkError) as e:
+        spk.spk_create(2, 1, spk.SPK_F32, 0, None)
+    assert e.value.code == spk.SPK_ERR_CUDA
+
+
+def test_package_has_no_oracle_dependency():
+    """The product package never reaches the oracle (test infrastructure only)."""
+    pdir = os.path.join(ROOT, "paper_2412_11639_gb300")
+    for dp, _, files in os.walk(pdir):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "oracle.c" not in txt, f
