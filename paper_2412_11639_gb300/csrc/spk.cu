@@ -53,8 +53,8 @@ struct Smem {
     uint8_t stage[NS][TT][ROW_BYTES];
     unsigned long long full[NS];
     unsigned long long empty[NS];
-    int rec_k[NCW][QCAP][32];
-    float rec_v[NCW][QCAP][32];
+    int rec_t[NCW][QCAP][32];
+    int rec_i[NCW][QCAP][32];
 };
 constexpr size_t SMEM_BYTES = sizeof(Smem) + 128;  // + alignment slack for the TMA tiles
 
@@ -156,105 +156,156 @@ __device__ __forceinline__ float seq_value(float theta, int n, int d) {
 }
 
 // --------------------------------------------------------------------- sinks ----
-// Frame records of one lane: (last frame index covered, value) in a per-lane queue.
+// Cuts of one lane, in time order, in a per-lane shared-memory ring of (t_cut, i_cut).
+// Stable spans run between consecutive cuts, so span j has N = i_j - i_{j-1} intervals
+// over D = t_j - t_{j-1} steps; the first starts at the first spike with index -1.  A
+// candidate that arrives one place early (a retroactive S_2 cut) is swapped in front of
+// the last cut.  Only cuts at or before the scan's frontier are final; the row flush
+// consumes nothing beyond the last final cut.  The pixel's last record is TAIL: it
+// holds the last value for the frames after the last spike (0 if there is no span).
+constexpr int TAIL = INT_MAX;
+
 template <typename OutT>
 struct FrameSink {
-    int *rk;       // &rec_k[warp][0][lane], slot stride 32
-    float *rv;
+    int *rt;       // &rec_t[warp][0][lane], slot stride 32
+    int *ri;
     OutT *col;     // out + p: frame k at col[k * P]
     int64_t P;
     float theta;
     int stride;
-    int head, tail;  // queue positions (monotone)
-    int F;           // frames < F are covered by pushed records
+    int T_out;
+    int head, tail;  // ring positions (monotone)
     int W;           // frames < W are written
-    float last_v;
+    int bad;         // set if a flush found no record for a frame (never expected)
+    int lt, li, lt2; // last cut (time, index) and the time of the one before (-1: none)
+    // cursor: the record at head spans (cur_ts, cur_te] with value cur_v; (cur_ts, cur_ti)
+    // is the previous cut (the first spike and -1 before the first record)
+    int cur_ts, cur_ti, cur_te, cur_ie;
+    float cur_v;
 
     __device__ __forceinline__ void store(int k, float v) { col[static_cast<int64_t>(k) * P] = to_out<OutT>(v); }
 
-    __device__ __forceinline__ void drain_one() {  // queue full: write the oldest record alone
+    __device__ __forceinline__ void load() {
         const int s = (head % QCAP) * 32;
-        const int kl = rk[s];
-        const float v = rv[s];
-        for (int k = W; k <= kl; ++k) store(k, v);
-        if (kl + 1 > W) W = kl + 1;
+        cur_te = rt[s];
+        cur_ie = ri[s];
+        if (cur_te != TAIL) cur_v = seq_value(theta, cur_ie - cur_ti, cur_te - cur_ts);
+    }
+    __device__ __forceinline__ void advance() {
+        cur_ts = cur_te;
+        cur_ti = cur_ie;
         ++head;
+        load();
     }
-    __device__ __forceinline__ void push(int kl, float v) {
+    // frames with t_k at or before the last final cut are resolved
+    __device__ __forceinline__ int resolved(int frontier) const {
+        const int ft = lt <= frontier ? lt : lt2;
+        if (ft == TAIL) return T_out;
+        return ft < 0 ? 0 : ft / stride + 1;
+    }
+    // write frame k, advancing over records that end before t_k
+    __device__ __forceinline__ void write_frame(int k) {
+        const int tk = k * stride;
+        while (tk > cur_te) {
+            if (head + 1 >= tail) {  // no record covers t_k: inconsistent, never expected
+                bad = 1;
+                return;
+            }
+            advance();
+        }
+        store(k, cur_v);
+    }
+    __device__ __forceinline__ void drain_one() {  // ring full: write the oldest (final) record alone
+        load();
+        const int kl = cur_te / stride;
+        for (int k = W; k <= kl; ++k) store(k, cur_v);
+        if (kl + 1 > W) W = kl + 1;
+        advance();
+    }
+    __device__ __forceinline__ void cand(int t, int i) {
         if (tail - head == QCAP) drain_one();
-        const int s = (tail % QCAP) * 32;
-        rk[s] = kl;
-        rv[s] = v;
+        if (tail > head && t < lt) {  // one place early: goes in front of the last cut
+            rt[((tail - 1) % QCAP) * 32] = t;
+            ri[((tail - 1) % QCAP) * 32] = i;
+            rt[(tail % QCAP) * 32] = lt;
+            ri[(tail % QCAP) * 32] = li;
+            lt2 = t;
+        } else {
+            rt[(tail % QCAP) * 32] = t;
+            ri[(tail % QCAP) * 32] = i;
+            lt2 = lt;
+            lt = t;
+            li = i;
+        }
         ++tail;
-        F = kl + 1;
-    }
-    __device__ __forceinline__ void operator()(int ts, int te, int n) {
-        const float v = seq_value(theta, n, te - ts);
-        last_v = v;
-        const int kl = te / stride;  // frames with t_k <= te
-        if (kl >= F) push(kl, v);
     }
 };
 
+// Verification sink: the spans themselves, in time order (a one-candidate hold restores
+// the order of a candidate that arrives one place early).
 struct SegSink {
     int32_t *ts, *te, *n;
     float *v;
     int64_t P, p;
     float theta;
     int cap, cnt;
-    __device__ __forceinline__ void operator()(int a, int b, int c) {
+    int ct, ci;        // last emitted cut (the first spike and -1 at the start)
+    int ht, hi, held;  // held candidate
+    __device__ __forceinline__ void emit(int t, int i) {
         if (cnt < cap) {
-            const int64_t i = static_cast<int64_t>(cnt) * P + p;
-            ts[i] = a;
-            te[i] = b;
-            n[i] = c;
-            v[i] = seq_value(theta, c, b - a);
+            const int64_t o = static_cast<int64_t>(cnt) * P + p;
+            ts[o] = ct;
+            te[o] = t;
+            n[o] = i - ci;
+            v[o] = seq_value(theta, i - ci, t - ct);
         }
         ++cnt;
+        ct = t;
+        ci = i;
+    }
+    __device__ __forceinline__ void cand(int t, int i) {
+        if (!held) {
+            ht = t;
+            hi = i;
+            held = 1;
+        } else if (t < ht) {
+            emit(t, i);
+        } else {
+            emit(ht, hi);
+            ht = t;
+            hi = i;
+        }
+    }
+    __device__ __forceinline__ void done() {
+        if (held) emit(ht, hi);
+        held = 0;
     }
 };
 
-// Warp-wide write of resolved frame rows.  Normal: rows below the warp minimum of F (full
-// rows).  Forced (a queue is nearly full, or the stream ended): every lane up to its own F.
+// Warp-wide write of resolved frame rows.  Normal: rows below the warp minimum of the
+// resolved counts (full rows).  Forced (a ring is nearly full, or the stream ended):
+// every lane up to its own resolved count.
 template <typename OutT>
-__device__ __forceinline__ void flush_rows(FrameSink<OutT> &sk, bool valid, bool final_flush) {
-    const int Fl = valid ? sk.F : INT_MAX;
+__device__ __forceinline__ void flush_rows(FrameSink<OutT> &sk, int frontier, bool valid, bool final_flush) {
+    const int F = valid ? sk.resolved(frontier) : INT_MAX;
     const int Wl = valid ? sk.W : INT_MAX;
     const int used = valid ? sk.tail - sk.head : 0;
-    const int Fmin = __reduce_min_sync(FULL, Fl);
+    const int Fmin = __reduce_min_sync(FULL, F);
     const int Wmin = __reduce_min_sync(FULL, Wl);
     const bool forced = final_flush || __reduce_max_sync(FULL, used) > QCAP - 8;
     int khi, lim;
     if (forced) {
-        khi = __reduce_max_sync(FULL, valid ? sk.F : 0);
-        lim = sk.F;
+        khi = __reduce_max_sync(FULL, valid ? F : 0);
+        lim = F;
     } else {
         khi = Fmin;
         lim = Fmin;
     }
     if (Wmin >= khi) return;  // nothing to write (warp-uniform)
-    int ck = INT_MAX;
-    float cv = 0.f;
-    if (valid && sk.head < sk.tail) {
-        const int s = (sk.head % QCAP) * 32;
-        ck = sk.rk[s];
-        cv = sk.rv[s];
-    }
-    for (int k = Wmin; k < khi; ++k) {
-        if (valid && k >= sk.W && k < lim) {
-            if (k > ck) {  // next record (each covers at least one frame)
-                ++sk.head;
-                const int s = (sk.head % QCAP) * 32;
-                ck = sk.rk[s];
-                cv = sk.rv[s];
-            }
-            sk.store(k, cv);
-        }
-    }
-    if (valid && lim > sk.W) {
-        sk.W = lim;
-        if (sk.head < sk.tail && ck < sk.W) ++sk.head;  // head record fully written
-    }
+    if (valid && sk.W < lim) sk.load();
+    for (int k = Wmin; k < khi; ++k)
+        if (valid && k >= sk.W && k < lim) sk.write_frame(k);
+    if (valid && lim > sk.W) sk.W = lim;
 }
 
 // ------------------------------------------------------------------- the kernel ----
@@ -301,16 +352,21 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     FrameSink<OutT> fs;
     SegSink ss;
     if constexpr (SEGMENTS) {
-        ss = SegSink{prm.seg_ts, prm.seg_te, prm.seg_n, prm.seg_v, prm.P, p, prm.theta, prm.cap, 0};
+        ss = SegSink{prm.seg_ts, prm.seg_te, prm.seg_n, prm.seg_v, prm.P, p, prm.theta, prm.cap, 0, 0, -1, 0, 0, 0};
     } else {
-        fs.rk = &sm.rec_k[warp][0][lane];
-        fs.rv = &sm.rec_v[warp][0][lane];
+        fs.rt = &sm.rec_t[warp][0][lane];
+        fs.ri = &sm.rec_i[warp][0][lane];
         fs.col = static_cast<OutT *>(prm.out) + (valid ? p : 0);
         fs.P = prm.P;
         fs.theta = prm.theta;
         fs.stride = prm.stride;
-        fs.head = fs.tail = fs.F = fs.W = 0;
-        fs.last_v = 0.f;
+        fs.T_out = prm.T_out;
+        fs.head = fs.tail = fs.W = fs.bad = 0;
+        fs.lt = fs.lt2 = -1;
+        fs.li = 0;
+        fs.cur_ts = fs.cur_te = 0;
+        fs.cur_ti = fs.cur_ie = -1;
+        fs.cur_v = 0.f;
     }
 
     bool ok = true;
@@ -332,29 +388,34 @@ __global__ void __launch_bounds__(NTHREADS, 3)
             if (!valid) w = 0;
             const int base = j * TT + h * 32;
             if (sc.last_t < 0 && w) {  // the stream's first spike opens the first sequence
-                sc.first_spike(base + __ffs(w) - 1);
+                const int t0 = base + __ffs(w) - 1;
+                sc.first_spike(t0);
+                if constexpr (SEGMENTS) ss.ct = t0;  // the first span starts here
+                else fs.cur_ts = t0;
                 w &= w - 1;
             }
+            if (w == 0xffffffffu && sc.absorb_ones(base)) w = 0;  // steady run of 1-intervals
             while (w) {
                 const int b = __ffs(w) - 1;
                 w &= w - 1;
                 if constexpr (SEGMENTS) sc.spike(base + b, ss);
                 else sc.spike(base + b, fs);
             }
-            if constexpr (!SEGMENTS) flush_rows(fs, valid, false);
+            if constexpr (!SEGMENTS) flush_rows(fs, sc.frontier(), valid, false);
         }
     }
     if (!ok) return;
 
     if constexpr (SEGMENTS) {
         sc.finish(ss);
+        ss.done();
         if (valid) prm.counts[p] = ss.cnt;
     } else {
         sc.finish(fs);
-        if (valid && fs.F < prm.T_out) fs.push(prm.T_out - 1, fs.last_v);  // tail hold
-        flush_rows(fs, valid, true);
+        if (valid) fs.cand(TAIL, 0);  // tail hold (0 without spans)
+        flush_rows(fs, INT_MAX, valid, true);
+        if (valid && fs.bad) atomicOr(prm.status, DEV_INTERNAL);
     }
-    if (valid && sc.err) atomicOr(prm.status, DEV_INTERNAL);
 }
 
 }  // namespace
