@@ -118,6 +118,38 @@ const char *spk_last_error(const spk_ctx *ctx);
 /* Number of kernel launches this context has issued since it was created. */
 int64_t spk_launch_count(const spk_ctx *ctx);
 
+/* Device scratch of spk_reconstruct_host_noalloc, in bytes (16 MiB). */
+#define SPK_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Host-buffer reconstruction that allocates nothing (the paper has no counterpart: this
+ * is a deployment variant of spk_reconstruct_host).
+ *
+ * Some callers cannot call cudaMalloc: processes whose device memory is owned entirely
+ * by another allocator or held to a fixed budget (an allocation outside it fails or is
+ * forbidden), and latency-critical camera loops that must not pay for an allocation or
+ * for the device-wide synchronisation a cudaFree implies.  This entry point needs no
+ * context (spk_create allocates) and stages the stream and the frames in one file-scope
+ * device array of SPK_NOALLOC_SCRATCH_BYTES that the library's module holds on every
+ * device it is loaded on, until the process exits.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ *   cfg           order, frame_stride, out_dtype, device and stream, as for spk_create
+ *                 (the stream must belong to cfg->device)
+ *   host_stream   host, uint8 [T][spk_pitch(H, W)]
+ *   host_frames   host, [T_out][H][W] of cfg->out_dtype, written completely
+ * The scratch holds a 256-byte status block, the stream rounded up to 256 bytes and the
+ * frames: 256 + round_up(T*pitch, 256) + T_out*H*W*sizeof(out) must not exceed
+ * SPK_NOALLOC_SCRATCH_BYTES, else the call returns SPK_ERR_ARG before any device work.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture begins.
+ * Every call shares the one array: a call clears the status word it needs, but two calls
+ * whose device work overlaps (other host threads, or other streams) race on the array
+ * and corrupt each other's results -- serialise them.  Synchronous: returns after the
+ * frames are in host_frames.  spk_last_error(NULL) describes a failure.
+ * Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_TIMEOUT, SPK_ERR_INTERNAL. */
+int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t *host_stream, int H, int W,
+                                 int T, float threshold, void *host_frames);
+
 #ifdef __cplusplus
 }
 #endif

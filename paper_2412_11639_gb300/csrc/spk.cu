@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/spk.h"
@@ -702,3 +703,110 @@ int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W,
 }
 
 }  // extern "C"
+
+// ============================================================ no-allocation variant ====
+// spk_reconstruct_host_noalloc: the stream and frames are staged in this file-scope
+// device array instead of context buffers.  In host code `g_noalloc_scratch` is only a
+// host-side stand-in for the symbol; the device address is looked up once per device
+// with cudaGetSymbolAddress and passed to the kernel.
+namespace {
+
+constexpr size_t NOALLOC_BYTES = SPK_NOALLOC_SCRATCH_BYTES;
+constexpr size_t NOALLOC_STATUS_BYTES = 256;  // status word, padded to keep 256-byte alignment
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[NOALLOC_MAX_DEVICES];  // device address per device, once looked up
+
+size_t round256(size_t n) { return (n + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t *host_stream, int H, int W,
+                                            int T, float threshold, void *host_frames) {
+    if (!cfg) return fail(nullptr, SPK_ERR_ARG, "cfg is NULL");
+    if (cfg->order != 1 && cfg->order != 2) return fail(nullptr, SPK_ERR_ARG, "order must be 1 or 2");
+    if (cfg->frame_stride < 1) return fail(nullptr, SPK_ERR_ARG, "frame_stride must be >= 1");
+    if (cfg->out_dtype != SPK_F32 && cfg->out_dtype != SPK_F16) return fail(nullptr, SPK_ERR_ARG, "bad out_dtype");
+    if (cfg->device < 0 || cfg->device >= NOALLOC_MAX_DEVICES) return fail(nullptr, SPK_ERR_ARG, "bad device ordinal");
+    if (!host_stream || !host_frames) return fail(nullptr, SPK_ERR_ARG, "host_stream or host_frames is NULL");
+    if (H <= 0 || W <= 0 || T <= 0) return fail(nullptr, SPK_ERR_ARG, "H, W, T must be > 0 (got %d, %d, %d)", H, W, T);
+    if (!std::isfinite(threshold) || !(threshold > 0.f))
+        return fail(nullptr, SPK_ERR_ARG, "threshold must be finite and > 0");
+    const int64_t P = static_cast<int64_t>(H) * W;
+    const int64_t T_out = spk_num_frames(T, cfg->frame_stride);
+    const size_t esz = cfg->out_dtype == SPK_F16 ? 2 : 4;
+    const double need_d = static_cast<double>(NOALLOC_STATUS_BYTES) +
+                          static_cast<double>(round256(static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W)))) +
+                          static_cast<double>(T_out) * static_cast<double>(P) * static_cast<double>(esz);
+    if (need_d > static_cast<double>(NOALLOC_BYTES))
+        return fail(nullptr, SPK_ERR_ARG,
+                    "stream + frames need %.0f bytes of device scratch; spk_reconstruct_host_noalloc has %zu "
+                    "(use spk_reconstruct_host for larger problems)",
+                    need_d, NOALLOC_BYTES);
+    const size_t in_bytes = static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W));
+    const size_t out_bytes = static_cast<size_t>(T_out) * static_cast<size_t>(P) * esz;
+
+    if (cudaSetDevice(cfg->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, SPK_ERR_CUDA, "cudaSetDevice(%d) failed", cfg->device);
+    }
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[cfg->device]) {  // set-up, once per device, with that device current
+            void *ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return fail(nullptr, SPK_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            }
+            g_noalloc_ptr[cfg->device] = static_cast<unsigned char *>(ptr);
+        }
+        base = g_noalloc_ptr[cfg->device];
+    }
+    int *d_status = reinterpret_cast<int *>(base);
+    uint8_t *d_in = base + NOALLOC_STATUS_BYTES;
+    void *d_out = base + NOALLOC_STATUS_BYTES + round256(in_bytes);
+
+    spk_ctx tmp{};  // host-side view for the shared launch path; owns no device memory
+    tmp.cfg = *cfg;
+    tmp.stream = static_cast<cudaStream_t>(cfg->stream);
+    tmp.d_status = d_status;
+    auto bail = [&](int code) {
+        snprintf(g_create_msg, sizeof(g_create_msg), "%s", tmp.msg);
+        return code;
+    };
+    // the array keeps the previous call's contents: clear the status word first
+    if (cudaMemsetAsync(d_status, 0, sizeof(int), tmp.stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_in, host_stream, in_bytes, cudaMemcpyHostToDevice, tmp.stream) != cudaSuccess) {
+        fail(&tmp, SPK_ERR_CUDA, "H2D staging: %s", cudaGetErrorString(cudaGetLastError()));
+        return bail(SPK_ERR_CUDA);
+    }
+    int rc = run_scan(&tmp, d_in, H, W, T, threshold, d_out, nullptr, nullptr, nullptr, nullptr, nullptr, 0, false);
+    if (rc) return bail(rc);
+    if (cudaMemcpyAsync(host_frames, d_out, out_bytes, cudaMemcpyDeviceToHost, tmp.stream) != cudaSuccess) {
+        fail(&tmp, SPK_ERR_CUDA, "D2H copy: %s", cudaGetErrorString(cudaGetLastError()));
+        return bail(SPK_ERR_CUDA);
+    }
+    cudaError_t e = cudaStreamSynchronize(tmp.stream);
+    if (e != cudaSuccess) {
+        fail(&tmp, SPK_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+        return bail(SPK_ERR_CUDA);
+    }
+    int st = 0;
+    if (cudaMemcpy(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        fail(&tmp, SPK_ERR_CUDA, "status read failed");
+        return bail(SPK_ERR_CUDA);
+    }
+    if (st & DEV_TIMEOUT) {
+        fail(&tmp, SPK_ERR_TIMEOUT, "a bounded device wait gave up");
+        return bail(SPK_ERR_TIMEOUT);
+    }
+    if (st) {
+        fail(&tmp, SPK_ERR_INTERNAL, "device consistency check failed (status %d)", st);
+        return bail(SPK_ERR_INTERNAL);
+    }
+    return SPK_OK;
+}

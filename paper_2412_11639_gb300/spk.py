@@ -17,7 +17,8 @@ SPK_F32, SPK_F16 = 0, 1
 _c = ctypes
 EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
            "spk_reconstruct_host", "spk_segments", "spk_synchronize", "spk_last_error",
-           "spk_launch_count")
+           "spk_launch_count", "spk_reconstruct_host_noalloc")
+SPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class SpkError(RuntimeError):
@@ -64,6 +65,8 @@ def load(path: str | None = None):
     lib.spk_last_error.restype = _c.c_char_p
     lib.spk_launch_count.argtypes = [vp]
     lib.spk_launch_count.restype = i64
+    lib.spk_reconstruct_host_noalloc.argtypes = [_c.POINTER(spk_config), vp, i32, i32, i32, f32, vp]
+    lib.spk_reconstruct_host_noalloc.restype = i32
     _lib = lib
     return lib
 
@@ -136,3 +139,13 @@ def spk_last_error(ctx) -> str:
 
 def spk_launch_count(ctx) -> int:
     return load().spk_launch_count(ctx)
+
+
+def spk_reconstruct_host_noalloc(host_stream, H, W, T, threshold, host_frames, order: int = 2,
+                                 frame_stride: int = 1, out_dtype: int = SPK_F32, device: int = 0,
+                                 stream: int | None = None):
+    """Host-buffer reconstruction staged in the library's fixed device array (no allocation)."""
+    cfg = spk_config(order, frame_stride, out_dtype, device, stream)
+    rc = load().spk_reconstruct_host_noalloc(_c.byref(cfg), _addr(host_stream), H, W, T, threshold,
+                                             _addr(host_frames))
+    return _check(None, rc)

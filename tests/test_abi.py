@@ -80,3 +80,17 @@ def test_package_has_no_oracle_dependency():
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "oracle.c" not in txt, f
+
+
+def test_noalloc_rejects_oversize_before_device_work(lib):
+    """The allocation-free entry point refuses problems beyond its fixed scratch."""
+    import numpy as np
+    st = np.zeros((4000, spk.spk_pitch(1000, 1000)), dtype=np.uint8)
+    out = np.zeros(1, dtype=np.float32)
+    with pytest.raises(spk.SpkError) as e:
+        spk.spk_reconstruct_host_noalloc(st, 1000, 1000, 4000, 1.0, out)
+    assert e.value.code == spk.SPK_ERR_ARG
+    assert "scratch" in str(e.value)
+    with pytest.raises(spk.SpkError) as e:
+        spk.spk_reconstruct_host_noalloc(st, 1, 8, 4, float("nan"), out)
+    assert e.value.code == spk.SPK_ERR_ARG
