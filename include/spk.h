@@ -118,6 +118,15 @@ const char *spk_last_error(const spk_ctx *ctx);
 /* Number of kernel launches this context has issued since it was created. */
 int64_t spk_launch_count(const spk_ctx *ctx);
 
+/* Diagnostic of the bounded device waits (no counterpart in the paper).  Every wait of
+ * the kernels (the mbarrier waits of the stream pipeline) gives up after a bounded time
+ * (about 2 s) instead of hanging, sets the timeout bit of the context's status word and
+ * returns.  This call launches one warp that waits, through the same code, on a barrier
+ * nothing will complete, with the limit limit_cycles (0 .. 4e9 SM clock cycles).  The
+ * following spk_synchronize(ctx) must return SPK_ERR_TIMEOUT, after which the context is
+ * usable again.  Asynchronous.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA. */
+int spk_selftest_wait(spk_ctx *ctx, int64_t limit_cycles);
+
 /* Device scratch of spk_reconstruct_host_noalloc, in bytes (16 MiB). */
 #define SPK_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -64,6 +64,8 @@ struct Params {
     int T;          // steps
     int ntiles;     // ceil(T / TT)
     int stride;     // frame stride
+    uint32_t div_m; // n / stride = umulhi(n, div_m) >> div_s for 0 <= n < 2^31 (stride >= 2)
+    int div_s;
     int T_out;      // frames
     float theta;    // threshold of Eq. 4
     void *out;      // frames [T_out][P]
@@ -110,11 +112,12 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
     return ok != 0;
 }
 // bounded wait: false (and the status word flagged) if the phase never completes
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int *status) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int *status,
+                                          long long limit = WAIT_CYCLES) {
     if (mbar_try_wait(bar, parity)) return true;
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > WAIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             atomicOr(status, DEV_TIMEOUT);
             return false;
         }
@@ -174,20 +177,26 @@ struct FrameSink {
     int64_t P;
     float theta;
     int stride;
+    uint32_t div_m;
+    int div_s;
     int T_out;
     int head, tail;  // ring positions (monotone)
+    int sorted;      // records before this position are in time order
     int W;           // frames < W are written
     int bad;         // set if a flush found no record for a frame (never expected)
-    int lt, li, lt2; // last cut (time, index) and the time of the one before (-1: none)
     // cursor: the record at head spans (cur_ts, cur_te] with value cur_v; (cur_ts, cur_ti)
     // is the previous cut (the first spike and -1 before the first record)
     int cur_ts, cur_ti, cur_te, cur_ie;
     float cur_v;
 
+    __device__ __forceinline__ int slot(int j) const { return (j & (QCAP - 1)) * 32; }
+    __device__ __forceinline__ int frame_of(int t) const {  // t / stride, t >= 0
+        return stride == 1 ? t : static_cast<int>(__umulhi(static_cast<uint32_t>(t), div_m) >> div_s);
+    }
     __device__ __forceinline__ void store(int k, float v) { col[static_cast<int64_t>(k) * P] = to_out<OutT>(v); }
 
     __device__ __forceinline__ void load() {
-        const int s = (head % QCAP) * 32;
+        const int s = slot(head);
         cur_te = rt[s];
         cur_ie = ri[s];
         if (cur_te != TAIL) cur_v = seq_value(theta, cur_ie - cur_ti, cur_te - cur_ts);
@@ -198,11 +207,29 @@ struct FrameSink {
         ++head;
         load();
     }
-    // frames with t_k at or before the last final cut are resolved
+    // A candidate that arrived one place early is swapped in front of its predecessor.
+    __device__ __forceinline__ void sort_new() {
+        for (int j = max(sorted - 1, head); j + 1 < tail; ++j) {
+            const int a = slot(j), b = slot(j + 1);
+            const int ta = rt[a], tb = rt[b];
+            if (tb < ta) {
+                const int ia = ri[a];
+                rt[a] = tb;
+                ri[a] = ri[b];
+                rt[b] = ta;
+                ri[b] = ia;
+            }
+        }
+        sorted = tail;
+    }
+    // frames with t_k at or before the last final cut are resolved (records sorted; the
+    // last record may be pending, the one before it is final)
     __device__ __forceinline__ int resolved(int frontier) const {
-        const int ft = lt <= frontier ? lt : lt2;
+        if (tail == head) return W;
+        int ft = rt[slot(tail - 1)];
+        if (ft > frontier) ft = tail - 1 > head ? rt[slot(tail - 2)] : -1;
         if (ft == TAIL) return T_out;
-        return ft < 0 ? 0 : ft / stride + 1;
+        return ft < 0 ? W : max(W, frame_of(ft) + 1);
     }
     // write frame k, advancing over records that end before t_k
     __device__ __forceinline__ void write_frame(int k) {
@@ -217,27 +244,18 @@ struct FrameSink {
         store(k, cur_v);
     }
     __device__ __forceinline__ void drain_one() {  // ring full: write the oldest (final) record alone
+        sort_new();
         load();
-        const int kl = cur_te / stride;
+        const int kl = frame_of(cur_te);
         for (int k = W; k <= kl; ++k) store(k, cur_v);
         if (kl + 1 > W) W = kl + 1;
         advance();
     }
     __device__ __forceinline__ void cand(int t, int i) {
         if (tail - head == QCAP) drain_one();
-        if (tail > head && t < lt) {  // one place early: goes in front of the last cut
-            rt[((tail - 1) % QCAP) * 32] = t;
-            ri[((tail - 1) % QCAP) * 32] = i;
-            rt[(tail % QCAP) * 32] = lt;
-            ri[(tail % QCAP) * 32] = li;
-            lt2 = t;
-        } else {
-            rt[(tail % QCAP) * 32] = t;
-            ri[(tail % QCAP) * 32] = i;
-            lt2 = lt;
-            lt = t;
-            li = i;
-        }
+        const int s = slot(tail);
+        rt[s] = t;
+        ri[s] = i;
         ++tail;
     }
 };
@@ -288,6 +306,7 @@ struct SegSink {
 // every lane up to its own resolved count.
 template <typename OutT>
 __device__ __forceinline__ void flush_rows(FrameSink<OutT> &sk, int frontier, bool valid, bool final_flush) {
+    if (valid && sk.sorted < sk.tail) sk.sort_new();
     const int F = valid ? sk.resolved(frontier) : INT_MAX;
     const int Wl = valid ? sk.W : INT_MAX;
     const int used = valid ? sk.tail - sk.head : 0;
@@ -362,9 +381,9 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         fs.theta = prm.theta;
         fs.stride = prm.stride;
         fs.T_out = prm.T_out;
-        fs.head = fs.tail = fs.W = fs.bad = 0;
-        fs.lt = fs.lt2 = -1;
-        fs.li = 0;
+        fs.div_m = prm.div_m;
+        fs.div_s = prm.div_s;
+        fs.head = fs.tail = fs.sorted = fs.W = fs.bad = 0;
         fs.cur_ts = fs.cur_te = 0;
         fs.cur_ti = fs.cur_ie = -1;
         fs.cur_v = 0.f;
@@ -417,6 +436,19 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         flush_rows(fs, INT_MAX, valid, true);
         if (valid && fs.bad) atomicOr(prm.status, DEV_INTERNAL);
     }
+}
+
+// Self-test of the bounded waits: one warp waits on an mbarrier that nothing arrives at,
+// through the same mbar_wait the scan uses, gives up after `limit` cycles and flags the
+// status word.
+__global__ void wait_selftest_kernel(int *status, long long limit) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    mbar_wait(&bar, 0, status, limit);
 }
 
 }  // namespace
@@ -533,6 +565,13 @@ int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float thr
     prm.T = T;
     prm.ntiles = (T + TT - 1) / TT;
     prm.stride = ctx->cfg.frame_stride;
+    if (prm.stride >= 2) {  // n / d = floor(m n / 2^(31 + l)), l = ceil(log2 d), m = ceil(2^(31+l) / d)
+        int l = 0;
+        while ((1LL << l) < prm.stride) ++l;
+        const unsigned long long m = ((1ULL << (31 + l)) + prm.stride - 1) / static_cast<unsigned long long>(prm.stride);
+        prm.div_m = static_cast<uint32_t>(m);
+        prm.div_s = l - 1;
+    }
     prm.T_out = static_cast<int>((static_cast<int64_t>(T) + prm.stride - 1) / prm.stride);
     prm.theta = threshold;
     prm.out = out;
@@ -657,6 +696,18 @@ int spk_synchronize(spk_ctx *ctx) {
         if (st & DEV_TIMEOUT) return fail(ctx, SPK_ERR_TIMEOUT, "a bounded device wait gave up");
         return fail(ctx, SPK_ERR_INTERNAL, "device consistency check failed (status %d)", st);
     }
+    return SPK_OK;
+}
+
+int spk_selftest_wait(spk_ctx *ctx, int64_t limit_cycles) {
+    if (!ctx) return SPK_ERR_ARG;
+    ctx->msg[0] = 0;
+    if (limit_cycles < 0 || limit_cycles > WAIT_CYCLES) return fail(ctx, SPK_ERR_ARG, "limit_cycles out of range");
+    cudaSetDevice(ctx->cfg.device);
+    wait_selftest_kernel<<<1, 32, 0, ctx->stream>>>(ctx->d_status, static_cast<long long>(limit_cycles));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    ++ctx->launches;
     return SPK_OK;
 }
 

@@ -17,7 +17,7 @@ SPK_F32, SPK_F16 = 0, 1
 _c = ctypes
 EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
            "spk_reconstruct_host", "spk_segments", "spk_synchronize", "spk_last_error",
-           "spk_launch_count", "spk_reconstruct_host_noalloc")
+           "spk_launch_count", "spk_reconstruct_host_noalloc", "spk_selftest_wait")
 SPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -65,6 +65,8 @@ def load(path: str | None = None):
     lib.spk_last_error.restype = _c.c_char_p
     lib.spk_launch_count.argtypes = [vp]
     lib.spk_launch_count.restype = i64
+    lib.spk_selftest_wait.argtypes = [vp, i64]
+    lib.spk_selftest_wait.restype = i32
     lib.spk_reconstruct_host_noalloc.argtypes = [_c.POINTER(spk_config), vp, i32, i32, i32, f32, vp]
     lib.spk_reconstruct_host_noalloc.restype = i32
     _lib = lib
@@ -139,6 +141,10 @@ def spk_last_error(ctx) -> str:
 
 def spk_launch_count(ctx) -> int:
     return load().spk_launch_count(ctx)
+
+
+def spk_selftest_wait(ctx, limit_cycles: int):
+    return _check(ctx, load().spk_selftest_wait(ctx, limit_cycles))
 
 
 def spk_reconstruct_host_noalloc(host_stream, H, W, T, threshold, host_frames, order: int = 2,
