@@ -95,6 +95,51 @@ int spk_reconstruct(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, fl
 int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W, int T,
                          float threshold, void *host_frames);
 
+/* A live stream: pushed piece by piece (spk_run), with its per-pixel scan state resident
+ * in device memory between pieces, so that pieces arriving over time give exactly the
+ * frames of one spk_reconstruct over the whole stream.  The FPGA of Sec. III-C carries the
+ * same state across its 32-frame chunks. */
+typedef struct spk_stream spk_stream;
+
+/* Opens a stream of H x W pixels and T steps on ctx (its order, frame stride, output type)
+ * and allocates its device state: 20 int32 per pixel (the stability scan, the frames
+ * already written, the cut that opens the current span, up to two pending cut
+ * candidates) and one int32.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM. */
+int spk_stream_open(spk_ctx *ctx, int H, int W, int T, spk_stream **out);
+
+/* Waits for ctx's stream and frees the stream's device state.  NULL is a no-op. */
+int spk_stream_close(spk_ctx *ctx, spk_stream *s);
+
+/* Steps pushed so far (the absolute step of the next piece's first row); -1 for NULL. */
+int64_t spk_stream_steps(const spk_stream *s);
+
+/* Waits for ctx's stream; *ready receives the number of leading frames that are final for
+ * every pixel after the last piece pushed (a frame is final once the stable span covering
+ * it has closed; all T_out frames after the last piece).  Errors: SPK_ERR_ARG, SPK_ERR_CUDA. */
+int spk_stream_ready(spk_ctx *ctx, const spk_stream *s, int64_t *ready);
+
+/* One unit of work for spk_run. */
+typedef struct spk_job {
+    const uint8_t *stream; /* device, uint8 [n][spk_pitch(H, W)], 16-byte aligned */
+    int H, W;              /* sensor rows and columns (must match `state` if given) */
+    int n;                 /* steps in this piece, > 0 */
+    float threshold;       /* as for spk_reconstruct; the same for every piece of a stream */
+    void *out_frames;      /* device, [T_out][H][W] of ctx's out_dtype, T_out frames of the whole
+                              stream; each frame is written at its absolute index */
+    spk_stream *state;     /* NULL: the piece is a whole stream of T = n steps.  Otherwise the
+                              piece holds steps [spk_stream_steps(state), ... + n) of that
+                              stream; the piece that reaches its T ends it (tail frames) */
+} spk_job;
+
+/* Runs every job in one kernel launch (at most 96 jobs per launch; larger calls are split
+ * into consecutive launches): the blocks of all jobs share the GPU, so many streams of
+ * uneven size and length -- and the next pieces of many live streams -- are processed
+ * together.  Each job gives the frames of Sec. III-B exactly as spk_reconstruct would.
+ * A stream may appear at most once per call; outputs of different jobs must not overlap.
+ * Asynchronous on ctx's stream.  Errors: SPK_ERR_ARG (bad job, piece past the stream's T,
+ * repeated stream), SPK_ERR_CUDA. */
+int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs);
+
 /* Verification export: the stable sequences themselves (the records the paper's FPGA
  * encoder emits, Sec. III-C).  For pixel p, counts[p] receives the number of sequences;
  * sequence j < cap is written at index j*H*W + p of t_start (spike time opening it),

@@ -10,12 +10,14 @@ from . import spk
 from .build import build
 from .spk import (SPK_F16, SPK_F32, SpkError, spk_create, spk_destroy, spk_launch_count,
                   spk_last_error, spk_num_frames, spk_pitch, spk_reconstruct,
-                  spk_reconstruct_host, spk_segments, spk_synchronize)
+                  spk_reconstruct_host, spk_run, spk_segments, spk_stream_close,
+                  spk_stream_open, spk_stream_ready, spk_stream_steps, spk_synchronize)
 
 __all__ = ["spk", "build", "Reconstructor", "SpkError", "SPK_F32", "SPK_F16", "spk_create",
            "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
            "spk_reconstruct_host", "spk_segments", "spk_synchronize", "spk_last_error",
-           "spk_launch_count"]
+           "spk_launch_count", "spk_run", "spk_stream_open", "spk_stream_close",
+           "spk_stream_ready", "spk_stream_steps", "Stream"]
 
 
 class Reconstructor:
@@ -77,3 +79,35 @@ class Reconstructor:
 
     def synchronize(self):
         spk_synchronize(self.ctx)
+
+
+class Stream:
+    """A live stream on a Reconstructor: per-pixel state stays on the device between pieces.
+
+    push(piece, n) reconstructs the next n steps (device uint8 [n][pitch]); frames go to
+    self.frames ([T_out][H][W]) at their absolute index; ready() is the number of leading
+    frames final for every pixel.
+    """
+
+    def __init__(self, rec: "Reconstructor", H: int, W: int, T: int, threshold: float = 1.0):
+        self.rec, self.H, self.W, self.T, self.threshold = rec, H, W, T, threshold
+        self.state = spk_stream_open(rec.ctx, H, W, T)
+        self.frames = rec.alloc_frames(H, W, T)
+
+    def job(self, piece, n: int):
+        return (piece, self.H, self.W, n, self.threshold, self.frames, self.state)
+
+    def push(self, piece, n: int):
+        spk_run(self.rec.ctx, [self.job(piece, n)])
+
+    @property
+    def steps(self) -> int:
+        return spk_stream_steps(self.state)
+
+    def ready(self) -> int:
+        return spk_stream_ready(self.rec.ctx, self.state)
+
+    def close(self):
+        if self.state is not None:
+            spk_stream_close(self.rec.ctx, self.state)
+            self.state = None

@@ -59,20 +59,38 @@ struct Smem {
 };
 constexpr size_t SMEM_BYTES = sizeof(Smem) + 128;  // + alignment slack for the TMA tiles
 
-struct Params {
+// One job: a piece of one stream (the whole stream, or the next steps of a live stream
+// whose per-pixel state is carried in device memory between launches).
+constexpr int JOB_FIRST = 1;  // the piece starts the stream (no carried state)
+constexpr int JOB_LAST = 2;   // the piece ends the stream (tail hold, every frame written)
+constexpr int CARRY_INTS = 20;  // carried state per pixel, stored [CARRY_INTS][P]
+
+struct Job {
     int64_t P;      // pixels
-    int T;          // steps
-    int ntiles;     // ceil(T / TT)
+    void *out;      // frames [T_out][P], absolute frame index
+    int *carry;     // [CARRY_INTS][P] (streams) or nullptr
+    int *ready;     // after the launch: min over pixels of frames written (streams) or nullptr
+    int n;          // steps in this piece (rows of its tensor map)
+    int ntiles;     // ceil(n / TT)
+    int t_base;     // absolute step of the piece's first row
+    int T_out;      // frames of the whole stream
     int stride;     // frame stride
-    uint32_t div_m; // n / stride = umulhi(n, div_m) >> div_s for 0 <= n < 2^31 (stride >= 2)
+    uint32_t div_m; // t / stride = umulhi(t, div_m) >> div_s for 0 <= t < 2^31 (stride >= 2)
     int div_s;
-    int T_out;      // frames
     float theta;    // threshold of Eq. 4
-    void *out;      // frames [T_out][P]
-    int32_t *counts, *seg_ts, *seg_te, *seg_n;  // segments mode
+    int flags;      // JOB_FIRST | JOB_LAST
+    int block0;     // first block of this job in the flat grid
+};
+
+template <int MAXJ>
+struct Batch {
+    CUtensorMap maps[MAXJ];  // one per job: the piece, [n][pitch] bytes
+    Job jobs[MAXJ];
+    int njobs;
+    int *status;
+    int32_t *counts, *seg_ts, *seg_te, *seg_n;  // segments mode (one job)
     float *seg_v;
     int cap;
-    int *status;
 };
 
 // ------------------------------------------------------------------ PTX helpers ----
@@ -329,14 +347,78 @@ __device__ __forceinline__ void flush_rows(FrameSink<OutT> &sk, int frontier, bo
 }
 
 // ------------------------------------------------------------------- the kernel ----
-template <int ORDER, typename OutT, bool SEGMENTS>
+// Carried state of one pixel between pieces of a stream: the scan registers, the frames
+// written, the last final cut (start of the open span) and up to two pending candidates.
+template <int ORDER, typename OutT>
+__device__ __forceinline__ void carry_load(const int *c, int64_t P, int64_t p, spk::PixelScan<ORDER> &sc,
+                                           FrameSink<OutT> &fs) {
+    c += p;
+    sc.last_t = c[0 * P];
+    sc.nint = c[1 * P];
+    sc.v0 = c[2 * P];
+    sc.v1 = c[3 * P];
+    sc.q0 = c[4 * P];
+    sc.tq0 = c[5 * P];
+    sc.dlo0 = c[6 * P];
+    sc.dhi0 = c[7 * P];
+    sc.q1 = c[8 * P];
+    sc.tq1 = c[9 * P];
+    sc.dlo1 = c[10 * P];
+    sc.dhi1 = c[11 * P];
+    fs.W = c[12 * P];
+    fs.cur_ts = fs.cur_te = c[13 * P];
+    fs.cur_ti = fs.cur_ie = c[14 * P];
+    const int npend = c[15 * P];
+    if (npend > 0) {
+        fs.rt[fs.slot(0)] = c[16 * P];
+        fs.ri[fs.slot(0)] = c[17 * P];
+    }
+    if (npend > 1) {
+        fs.rt[fs.slot(1)] = c[18 * P];
+        fs.ri[fs.slot(1)] = c[19 * P];
+    }
+    fs.tail = fs.sorted = npend;
+}
+
+template <int ORDER, typename OutT>
+__device__ __forceinline__ void carry_store(int *c, int64_t P, int64_t p, const spk::PixelScan<ORDER> &sc,
+                                            const FrameSink<OutT> &fs, int npend, int pj) {
+    c += p;
+    c[0 * P] = sc.last_t;
+    c[1 * P] = sc.nint;
+    c[2 * P] = sc.v0;
+    c[3 * P] = sc.v1;
+    c[4 * P] = sc.q0;
+    c[5 * P] = sc.tq0;
+    c[6 * P] = sc.dlo0;
+    c[7 * P] = sc.dhi0;
+    c[8 * P] = sc.q1;
+    c[9 * P] = sc.tq1;
+    c[10 * P] = sc.dlo1;
+    c[11 * P] = sc.dhi1;
+    c[12 * P] = fs.W;
+    c[13 * P] = fs.cur_ts;
+    c[14 * P] = fs.cur_ti;
+    c[15 * P] = npend;
+    c[16 * P] = npend > 0 ? fs.rt[fs.slot(pj)] : 0;
+    c[17 * P] = npend > 0 ? fs.ri[fs.slot(pj)] : 0;
+    c[18 * P] = npend > 1 ? fs.rt[fs.slot(pj + 1)] : 0;
+    c[19 * P] = npend > 1 ? fs.ri[fs.slot(pj + 1)] : 0;
+}
+
+template <int ORDER, typename OutT, bool SEGMENTS, int MAXJ>
 __global__ void __launch_bounds__(NTHREADS, 3)
-    spk_scan_kernel(const __grid_constant__ CUtensorMap tmap, const Params prm) {
+    spk_scan_kernel(const __grid_constant__ Batch<MAXJ> prm) {
     extern __shared__ uint8_t smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+    __shared__ int s_job;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
+        int jb = 0;  // the job whose block range holds this block
+        for (int k = 1; k < prm.njobs; ++k)
+            if (static_cast<int>(blockIdx.x) >= prm.jobs[k].block0) jb = k;
+        s_job = jb;
         for (int s = 0; s < NS; ++s) {
             mbar_init(&sm.full[s], 1);
             mbar_init(&sm.empty[s], NCW * 32);  // every consumer lane releases
@@ -344,16 +426,20 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    const int jb = s_job;
+    const Job &job = prm.jobs[jb];
+    const int blk = static_cast<int>(blockIdx.x) - job.block0;  // block within the job
 
     if (warp == NCW) {  // ---------------------------------------- producer warp ----
         if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+            const CUtensorMap *map = &prm.maps[jb];
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
             int issued = 0;
-            for (int j = 0; j < prm.ntiles; ++j) {
+            for (int j = 0; j < job.ntiles; ++j) {
                 const int s = j % NS;
                 if (j >= NS && !mbar_wait(&sm.empty[s], ((j / NS) - 1) & 1, prm.status)) break;
                 mbar_arrive_expect_tx(&sm.full[s], TT * ROW_BYTES);
-                tma_load_2d(&sm.stage[s][0][0], &tmap, &sm.full[s], blockIdx.x * ROW_BYTES, j * TT);
+                tma_load_2d(&sm.stage[s][0][0], map, &sm.full[s], blk * ROW_BYTES, j * TT);
                 issued = j + 1;
             }
             // let every copy land before this warp leaves (matters only after an error)
@@ -364,33 +450,34 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     }
 
     // ------------------------------------------------------------- compute warps ----
-    const int64_t p = static_cast<int64_t>(blockIdx.x) * BLOCK_PIX + warp * 32 + lane;
-    const bool valid = p < prm.P;
+    const int64_t p = static_cast<int64_t>(blk) * BLOCK_PIX + warp * 32 + lane;
+    const bool valid = p < job.P;
     spk::PixelScan<ORDER> sc;
     sc.init();
 
     FrameSink<OutT> fs;
     SegSink ss;
     if constexpr (SEGMENTS) {
-        ss = SegSink{prm.seg_ts, prm.seg_te, prm.seg_n, prm.seg_v, prm.P, p, prm.theta, prm.cap, 0, 0, -1, 0, 0, 0};
+        ss = SegSink{prm.seg_ts, prm.seg_te, prm.seg_n, prm.seg_v, job.P, p, job.theta, prm.cap, 0, 0, -1, 0, 0, 0};
     } else {
         fs.rt = &sm.rec_t[warp][0][lane];
         fs.ri = &sm.rec_i[warp][0][lane];
-        fs.col = static_cast<OutT *>(prm.out) + (valid ? p : 0);
-        fs.P = prm.P;
-        fs.theta = prm.theta;
-        fs.stride = prm.stride;
-        fs.T_out = prm.T_out;
-        fs.div_m = prm.div_m;
-        fs.div_s = prm.div_s;
+        fs.col = static_cast<OutT *>(job.out) + (valid ? p : 0);
+        fs.P = job.P;
+        fs.theta = job.theta;
+        fs.stride = job.stride;
+        fs.T_out = job.T_out;
+        fs.div_m = job.div_m;
+        fs.div_s = job.div_s;
         fs.head = fs.tail = fs.sorted = fs.W = fs.bad = 0;
         fs.cur_ts = fs.cur_te = 0;
         fs.cur_ti = fs.cur_ie = -1;
         fs.cur_v = 0.f;
+        if (!(job.flags & JOB_FIRST) && valid) carry_load(job.carry, job.P, p, sc, fs);
     }
 
     bool ok = true;
-    for (int j = 0; j < prm.ntiles; ++j) {
+    for (int j = 0; j < job.ntiles; ++j) {
         const int s = j % NS;
         // warp-uniform outcome: every lane leaves together if any lane's wait gave up
         if (!__all_sync(FULL, mbar_wait(&sm.full[s], (j / NS) & 1, prm.status))) {
@@ -406,7 +493,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         for (int h = 0; h < 2; ++h) {
             uint32_t w = warp_transpose32(h ? r1 : r0, lane);
             if (!valid) w = 0;
-            const int base = j * TT + h * 32;
+            const int base = job.t_base + j * TT + h * 32;
             if (sc.last_t < 0 && w) {  // the stream's first spike opens the first sequence
                 const int t0 = base + __ffs(w) - 1;
                 sc.first_spike(t0);
@@ -430,11 +517,35 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         sc.finish(ss);
         ss.done();
         if (valid) prm.counts[p] = ss.cnt;
-    } else {
+    } else if (job.flags & JOB_LAST) {
         sc.finish(fs);
         if (valid) fs.cand(TAIL, 0);  // tail hold (0 without spans)
         flush_rows(fs, INT_MAX, valid, true);
         if (valid && fs.bad) atomicOr(prm.status, DEV_INTERNAL);
+    } else {
+        // piece end: write every resolved frame, fold the final cuts into the start of the
+        // open span, keep the pending candidates
+        if (valid) fs.sort_new();
+        const int S = sc.frontier();
+        flush_rows(fs, S, valid, true);
+        int j = fs.head;
+        if (valid) {
+            for (; j < fs.tail; ++j) {
+                const int t = fs.rt[fs.slot(j)];
+                if (t > S) break;
+                fs.cur_ts = t;
+                fs.cur_ti = fs.ri[fs.slot(j)];
+            }
+            const int npend = fs.tail - j;
+            if (npend > 2 || fs.bad) atomicOr(prm.status, DEV_INTERNAL);
+            carry_store(job.carry, job.P, p, sc, fs, npend > 2 ? 2 : npend, j);
+        }
+    }
+    if constexpr (!SEGMENTS) {
+        if (job.ready) {  // frames written for every pixel of the stream
+            const int wmin = __reduce_min_sync(FULL, valid ? fs.W : INT_MAX);
+            if (lane == 0) atomicMin(job.ready, wmin);
+        }
     }
 }
 
@@ -454,6 +565,14 @@ __global__ void wait_selftest_kernel(int *status, long long limit) {
 }  // namespace
 
 // ========================================================================= host ====
+struct spk_stream {
+    int H, W, T;
+    int64_t pushed;  // steps pushed so far
+    int device;
+    int *d_carry;    // [CARRY_INTS][H*W]
+    int *d_ready;    // min over pixels of frames written, after the last push
+};
+
 struct spk_ctx {
     spk_config cfg;
     cudaStream_t stream;
@@ -521,10 +640,10 @@ int check_stream_args(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, 
     return SPK_OK;
 }
 
-int make_tmap(spk_ctx *ctx, CUtensorMap *map, const uint8_t *stream, int64_t pitch, int T) {
+int make_tmap(spk_ctx *ctx, CUtensorMap *map, const uint8_t *stream, int64_t pitch, int rows) {
     auto enc = get_encode();
     if (!enc) return fail(ctx, SPK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-    cuuint64_t dims[2] = {static_cast<cuuint64_t>(pitch), static_cast<cuuint64_t>(T)};
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(pitch), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch)};
     cuuint32_t box[2] = {ROW_BYTES, TT};
     cuuint32_t estr[2] = {1, 1};
@@ -535,58 +654,75 @@ int make_tmap(spk_ctx *ctx, CUtensorMap *map, const uint8_t *stream, int64_t pit
     return SPK_OK;
 }
 
-template <int ORDER, typename OutT, bool SEG>
-int launch(spk_ctx *ctx, const CUtensorMap &map, const Params &prm) {
-    auto kern = spk_scan_kernel<ORDER, OutT, SEG>;
-    static bool attr_done = false;  // per instantiation
-    if (!attr_done) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
-            return fail(ctx, SPK_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(cudaGetLastError()));
-        attr_done = true;
-    }
-    const int64_t nblk = (prm.P + BLOCK_PIX - 1) / BLOCK_PIX;
-    kern<<<static_cast<unsigned>(nblk), NTHREADS, SMEM_BYTES, ctx->stream>>>(map, prm);
+constexpr int MAXJ_BATCH = 96;  // jobs per launch (kernel parameters stay under 32 KB)
+
+template <int ORDER, typename OutT, bool SEG, int MAXJ>
+int launch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
+    auto kern = spk_scan_kernel<ORDER, OutT, SEG, MAXJ>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(cudaGetLastError()));
+    kern<<<static_cast<unsigned>(nblocks), NTHREADS, SMEM_BYTES, ctx->stream>>>(prm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
     ++ctx->launches;
     return SPK_OK;
 }
 
+template <int MAXJ>
+int dispatch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks, bool segments) {
+    const int order = ctx->cfg.order;
+    if (segments) return order == 1 ? launch<1, float, true>(ctx, prm, nblocks) : launch<2, float, true>(ctx, prm, nblocks);
+    if (ctx->cfg.out_dtype == SPK_F16)
+        return order == 1 ? launch<1, __half, false>(ctx, prm, nblocks) : launch<2, __half, false>(ctx, prm, nblocks);
+    return order == 1 ? launch<1, float, false>(ctx, prm, nblocks) : launch<2, float, false>(ctx, prm, nblocks);
+}
+
+// one job's kernel parameters; returns its block count (or a negative error)
+int fill_job(spk_ctx *ctx, CUtensorMap *map, Job *job, const uint8_t *stream, int H, int W, int n, int t_base,
+             int T, float threshold, void *out, int *carry, int *ready, int flags, int block0) {
+    const int64_t P = static_cast<int64_t>(H) * W;
+    int rc = make_tmap(ctx, map, stream, pitch_of(H, W), n);
+    if (rc) return rc;
+    *job = Job{};
+    job->P = P;
+    job->out = out;
+    job->carry = carry;
+    job->ready = ready;
+    job->n = n;
+    job->ntiles = (n + TT - 1) / TT;
+    job->t_base = t_base;
+    job->stride = ctx->cfg.frame_stride;
+    job->T_out = static_cast<int>((static_cast<int64_t>(T) + job->stride - 1) / job->stride);
+    if (job->stride >= 2) {  // t / d = floor(m t / 2^(31 + l)), l = ceil(log2 d), m = ceil(2^(31+l) / d)
+        int l = 0;
+        while ((1LL << l) < job->stride) ++l;
+        const unsigned long long m =
+            ((1ULL << (31 + l)) + job->stride - 1) / static_cast<unsigned long long>(job->stride);
+        job->div_m = static_cast<uint32_t>(m);
+        job->div_s = l - 1;
+    }
+    job->theta = threshold;
+    job->flags = flags;
+    job->block0 = block0;
+    return static_cast<int>((P + BLOCK_PIX - 1) / BLOCK_PIX);
+}
+
 int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold, void *out,
              int32_t *counts, int32_t *ts, int32_t *te, int32_t *n, float *v, int cap, bool segments) {
-    const int64_t P = static_cast<int64_t>(H) * W;
-    const int64_t pitch = pitch_of(H, W);
-    CUtensorMap map;
-    int rc = make_tmap(ctx, &map, stream, pitch, T);
-    if (rc) return rc;
     if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
-    Params prm{};
-    prm.P = P;
-    prm.T = T;
-    prm.ntiles = (T + TT - 1) / TT;
-    prm.stride = ctx->cfg.frame_stride;
-    if (prm.stride >= 2) {  // n / d = floor(m n / 2^(31 + l)), l = ceil(log2 d), m = ceil(2^(31+l) / d)
-        int l = 0;
-        while ((1LL << l) < prm.stride) ++l;
-        const unsigned long long m = ((1ULL << (31 + l)) + prm.stride - 1) / static_cast<unsigned long long>(prm.stride);
-        prm.div_m = static_cast<uint32_t>(m);
-        prm.div_s = l - 1;
-    }
-    prm.T_out = static_cast<int>((static_cast<int64_t>(T) + prm.stride - 1) / prm.stride);
-    prm.theta = threshold;
-    prm.out = out;
+    Batch<1> prm{};
+    const int nb = fill_job(ctx, &prm.maps[0], &prm.jobs[0], stream, H, W, T, 0, T, threshold, out, nullptr,
+                            nullptr, JOB_FIRST | JOB_LAST, 0);
+    if (nb < 0) return nb;
+    prm.njobs = 1;
+    prm.status = ctx->d_status;
     prm.counts = counts;
     prm.seg_ts = ts;
     prm.seg_te = te;
     prm.seg_n = n;
     prm.seg_v = v;
     prm.cap = cap;
-    prm.status = ctx->d_status;
-    const int order = ctx->cfg.order;
-    if (segments) return order == 1 ? launch<1, float, true>(ctx, map, prm) : launch<2, float, true>(ctx, map, prm);
-    if (ctx->cfg.out_dtype == SPK_F16)
-        return order == 1 ? launch<1, __half, false>(ctx, map, prm) : launch<2, __half, false>(ctx, map, prm);
-    return order == 1 ? launch<1, float, false>(ctx, map, prm) : launch<2, float, false>(ctx, map, prm);
+    return dispatch(ctx, prm, nb, segments);
 }
 
 bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
@@ -697,6 +833,126 @@ int spk_synchronize(spk_ctx *ctx) {
         return fail(ctx, SPK_ERR_INTERNAL, "device consistency check failed (status %d)", st);
     }
     return SPK_OK;
+}
+
+int spk_stream_open(spk_ctx *ctx, int H, int W, int T, spk_stream **out) {
+    if (!ctx) return SPK_ERR_ARG;
+    ctx->msg[0] = 0;
+    if (!out) return fail(ctx, SPK_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (H <= 0 || W <= 0 || T <= 0 || T > (1 << 30)) return fail(ctx, SPK_ERR_ARG, "bad H, W or T");
+    if (static_cast<int64_t>(H) * W > (1LL << 31) - BLOCK_PIX) return fail(ctx, SPK_ERR_ARG, "H*W too large");
+    if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
+    spk_stream *st = new (std::nothrow) spk_stream();
+    if (!st) return fail(ctx, SPK_ERR_OOM, "host allocation failed");
+    st->H = H;
+    st->W = W;
+    st->T = T;
+    st->device = ctx->cfg.device;
+    const size_t carry_bytes = static_cast<size_t>(CARRY_INTS) * static_cast<size_t>(H) * static_cast<size_t>(W) * 4;
+    if (cudaMalloc(&st->d_carry, carry_bytes) != cudaSuccess || cudaMalloc(&st->d_ready, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (st->d_carry) cudaFree(st->d_carry);
+        delete st;
+        return fail(ctx, SPK_ERR_OOM, "cudaMalloc of the stream state failed");
+    }
+    if (cudaMemsetAsync(st->d_ready, 0, sizeof(int), ctx->stream) != cudaSuccess) {
+        cudaFree(st->d_carry);
+        cudaFree(st->d_ready);
+        delete st;
+        return fail(ctx, SPK_ERR_CUDA, "cudaMemsetAsync failed");
+    }
+    *out = st;
+    return SPK_OK;
+}
+
+int spk_stream_close(spk_ctx *ctx, spk_stream *s) {
+    if (!s) return SPK_OK;
+    if (ctx) {
+        cudaSetDevice(ctx->cfg.device);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    cudaFree(s->d_carry);
+    cudaFree(s->d_ready);
+    delete s;
+    return SPK_OK;
+}
+
+int64_t spk_stream_steps(const spk_stream *s) { return s ? s->pushed : -1; }
+
+int spk_stream_ready(spk_ctx *ctx, const spk_stream *s, int64_t *ready) {
+    if (!ctx || !s || !ready) return ctx ? fail(ctx, SPK_ERR_ARG, "NULL argument") : SPK_ERR_ARG;
+    cudaSetDevice(ctx->cfg.device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    int r = 0;
+    if (cudaMemcpy(&r, s->d_ready, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "ready read failed");
+    *ready = r;
+    return SPK_OK;
+}
+
+int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
+    if (!ctx) return SPK_ERR_ARG;
+    ctx->msg[0] = 0;
+    if (njobs < 0 || (njobs > 0 && !jobs)) return fail(ctx, SPK_ERR_ARG, "bad job list");
+    const size_t esz = ctx->cfg.out_dtype == SPK_F16 ? 2 : 4;
+    for (int k = 0; k < njobs; ++k) {  // validate everything before any launch
+        const spk_job &jb = jobs[k];
+        int rc = check_stream_args(ctx, jb.stream, jb.H, jb.W, jb.n, jb.threshold);
+        if (rc) return rc;
+        if (!jb.out_frames || reinterpret_cast<uintptr_t>(jb.out_frames) % 16)
+            return fail(ctx, SPK_ERR_ARG, "job %d: out_frames is NULL or not 16-byte aligned", k);
+        const int T = jb.state ? jb.state->T : jb.n;
+        const size_t out_bytes = static_cast<size_t>(spk_num_frames(T, ctx->cfg.frame_stride)) *
+                                 static_cast<size_t>(jb.H) * static_cast<size_t>(jb.W) * esz;
+        const size_t in_bytes = static_cast<size_t>(jb.n) * static_cast<size_t>(pitch_of(jb.H, jb.W));
+        if (overlaps(jb.stream, in_bytes, jb.out_frames, out_bytes))
+            return fail(ctx, SPK_ERR_ARG, "job %d: out_frames overlaps its stream", k);
+        if (!is_device_ptr(jb.stream) || !is_device_ptr(jb.out_frames))
+            return fail(ctx, SPK_ERR_ARG, "job %d: stream and out_frames must be device memory", k);
+        if (jb.state) {
+            if (jb.state->H != jb.H || jb.state->W != jb.W) return fail(ctx, SPK_ERR_ARG, "job %d: H, W differ from its stream", k);
+            if (jb.state->pushed + jb.n > jb.state->T) return fail(ctx, SPK_ERR_ARG, "job %d: piece runs past the stream's T", k);
+            if (jb.state->device != ctx->cfg.device) return fail(ctx, SPK_ERR_ARG, "job %d: stream on another device", k);
+            for (int m = 0; m < k; ++m)
+                if (jobs[m].state == jb.state) return fail(ctx, SPK_ERR_ARG, "jobs %d and %d push the same stream", m, k);
+        }
+    }
+    if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
+    Batch<MAXJ_BATCH> *prm = new (std::nothrow) Batch<MAXJ_BATCH>();
+    if (!prm) return fail(ctx, SPK_ERR_OOM, "host allocation failed");
+    int rc = SPK_OK;
+    for (int k0 = 0; k0 < njobs && rc == SPK_OK; k0 += MAXJ_BATCH) {
+        const int nj = njobs - k0 < MAXJ_BATCH ? njobs - k0 : MAXJ_BATCH;
+        int blocks = 0;
+        for (int k = 0; k < nj && rc == SPK_OK; ++k) {
+            const spk_job &jb = jobs[k0 + k];
+            spk_stream *st = jb.state;
+            int flags = JOB_FIRST | JOB_LAST, t_base = 0, T = jb.n;
+            if (st) {
+                t_base = static_cast<int>(st->pushed);
+                T = st->T;
+                flags = (st->pushed == 0 ? JOB_FIRST : 0) | (st->pushed + jb.n == st->T ? JOB_LAST : 0);
+                if (cudaMemsetAsync(st->d_ready, 0x7f, sizeof(int), ctx->stream) != cudaSuccess)
+                    rc = fail(ctx, SPK_ERR_CUDA, "cudaMemsetAsync failed");
+            }
+            const int nb = fill_job(ctx, &prm->maps[k], &prm->jobs[k], jb.stream, jb.H, jb.W, jb.n, t_base, T,
+                                    jb.threshold, jb.out_frames, st ? st->d_carry : nullptr,
+                                    st ? st->d_ready : nullptr, flags, blocks);
+            if (nb < 0) rc = nb;
+            else blocks += nb;
+        }
+        if (rc) break;
+        prm->njobs = nj;
+        prm->status = ctx->d_status;
+        rc = dispatch(ctx, *prm, blocks, false);
+        if (rc == SPK_OK)
+            for (int k = 0; k < nj; ++k)
+                if (jobs[k0 + k].state) jobs[k0 + k].state->pushed += jobs[k0 + k].n;
+    }
+    delete prm;
+    return rc;
 }
 
 int spk_selftest_wait(spk_ctx *ctx, int64_t limit_cycles) {

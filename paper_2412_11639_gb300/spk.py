@@ -17,7 +17,8 @@ SPK_F32, SPK_F16 = 0, 1
 _c = ctypes
 EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
            "spk_reconstruct_host", "spk_segments", "spk_synchronize", "spk_last_error",
-           "spk_launch_count", "spk_reconstruct_host_noalloc", "spk_selftest_wait")
+           "spk_launch_count", "spk_reconstruct_host_noalloc", "spk_selftest_wait", "spk_stream_open",
+           "spk_stream_close", "spk_stream_steps", "spk_stream_ready", "spk_run")
 SPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -30,6 +31,11 @@ class SpkError(RuntimeError):
 class spk_config(ctypes.Structure):
     _fields_ = [("order", _c.c_int), ("frame_stride", _c.c_int), ("out_dtype", _c.c_int),
                 ("device", _c.c_int), ("stream", _c.c_void_p)]
+
+
+class spk_job(ctypes.Structure):
+    _fields_ = [("stream", _c.c_void_p), ("H", _c.c_int), ("W", _c.c_int), ("n", _c.c_int),
+                ("threshold", _c.c_float), ("out_frames", _c.c_void_p), ("state", _c.c_void_p)]
 
 
 _lib = None
@@ -65,6 +71,16 @@ def load(path: str | None = None):
     lib.spk_last_error.restype = _c.c_char_p
     lib.spk_launch_count.argtypes = [vp]
     lib.spk_launch_count.restype = i64
+    lib.spk_stream_open.argtypes = [vp, i32, i32, i32, _c.POINTER(vp)]
+    lib.spk_stream_open.restype = i32
+    lib.spk_stream_close.argtypes = [vp, vp]
+    lib.spk_stream_close.restype = i32
+    lib.spk_stream_steps.argtypes = [vp]
+    lib.spk_stream_steps.restype = i64
+    lib.spk_stream_ready.argtypes = [vp, vp, _c.POINTER(i64)]
+    lib.spk_stream_ready.restype = i32
+    lib.spk_run.argtypes = [vp, _c.POINTER(spk_job), i32]
+    lib.spk_run.restype = i32
     lib.spk_selftest_wait.argtypes = [vp, i64]
     lib.spk_selftest_wait.restype = i32
     lib.spk_reconstruct_host_noalloc.argtypes = [_c.POINTER(spk_config), vp, i32, i32, i32, f32, vp]
@@ -155,3 +171,31 @@ def spk_reconstruct_host_noalloc(host_stream, H, W, T, threshold, host_frames, o
     rc = load().spk_reconstruct_host_noalloc(_c.byref(cfg), _addr(host_stream), H, W, T, threshold,
                                              _addr(host_frames))
     return _check(None, rc)
+
+
+def spk_stream_open(ctx, H: int, W: int, T: int):
+    out = _c.c_void_p()
+    _check(ctx, load().spk_stream_open(ctx, H, W, T, _c.byref(out)))
+    return out
+
+
+def spk_stream_close(ctx, state):
+    return load().spk_stream_close(ctx, state)
+
+
+def spk_stream_steps(state) -> int:
+    return load().spk_stream_steps(state)
+
+
+def spk_stream_ready(ctx, state) -> int:
+    r = _c.c_int64()
+    _check(ctx, load().spk_stream_ready(ctx, state, _c.byref(r)))
+    return r.value
+
+
+def spk_run(ctx, jobs):
+    """jobs: sequence of (stream, H, W, n, threshold, out_frames, state_or_None)."""
+    arr = (spk_job * len(jobs))()
+    for k, (st, H, W, n, th, out, state) in enumerate(jobs):
+        arr[k] = spk_job(_addr(st), H, W, n, th, _addr(out), state)
+    return _check(ctx, load().spk_run(ctx, arr, len(jobs)))
