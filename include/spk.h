@@ -140,6 +140,19 @@ typedef struct spk_job {
  * repeated stream), SPK_ERR_CUDA. */
 int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs);
 
+/* Time tile of the frames kernels: the steps one TMA box stages per block (32, 64 or 128;
+ * 64 by default).  Results do not depend on it; speed does.  Errors: SPK_ERR_ARG. */
+int spk_set_tile(spk_ctx *ctx, int tile);
+
+/* The context's current time tile; -1 for NULL. */
+int spk_get_tile(const spk_ctx *ctx);
+
+/* Autotuner: runs the given whole-stream jobs (state == NULL; they are run repeatedly)
+ * once to warm up and three times timed with each time tile, keeps the fastest in ctx and
+ * returns it in *best_tile (may be NULL).  Synchronous.  Errors: as spk_run, and
+ * SPK_ERR_ARG for stream jobs. */
+int spk_autotune(spk_ctx *ctx, const spk_job *jobs, int njobs, int *best_tile);
+
 /* Verification export: the stable sequences themselves (the records the paper's FPGA
  * encoder emits, Sec. III-C).  For pixel p, counts[p] receives the number of sequences;
  * sequence j < cap is written at index j*H*W + p of t_start (spike time opening it),

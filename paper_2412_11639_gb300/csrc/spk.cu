@@ -39,7 +39,7 @@ namespace {
 constexpr int NCW = 8;                   // compute warps per block
 constexpr int BLOCK_PIX = NCW * 32;      // pixels per block
 constexpr int ROW_BYTES = BLOCK_PIX / 8; // bytes of one frame row per block (TMA box x)
-constexpr int TT = 64;                   // steps per TMA tile (box y)
+constexpr int TT_DEFAULT = 64;           // steps per TMA tile (box y); 32, 64 or 128
 constexpr int NS = 4;                    // pipeline stages
 constexpr int QCAP = 32;                 // records per lane
 constexpr int NTHREADS = (NCW + 1) * 32; // + one producer warp
@@ -50,6 +50,7 @@ constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bounded waits
 constexpr int DEV_TIMEOUT = 1;
 constexpr int DEV_INTERNAL = 2;
 
+template <int TT>
 struct Smem {
     uint8_t stage[NS][TT][ROW_BYTES];
     unsigned long long full[NS];
@@ -57,7 +58,8 @@ struct Smem {
     int rec_t[NCW][QCAP][32];
     int rec_i[NCW][QCAP][32];
 };
-constexpr size_t SMEM_BYTES = sizeof(Smem) + 128;  // + alignment slack for the TMA tiles
+template <int TT>
+constexpr size_t smem_bytes() { return sizeof(Smem<TT>) + 128; }  // + alignment slack for TMA
 
 // One job: a piece of one stream (the whole stream, or the next steps of a live stream
 // whose per-pixel state is carried in device memory between launches).
@@ -71,7 +73,7 @@ struct Job {
     int *carry;     // [CARRY_INTS][P] (streams) or nullptr
     int *ready;     // after the launch: min over pixels of frames written (streams) or nullptr
     int n;          // steps in this piece (rows of its tensor map)
-    int ntiles;     // ceil(n / TT)
+    int ntiles;     // ceil(n / tile)
     int t_base;     // absolute step of the piece's first row
     int T_out;      // frames of the whole stream
     int stride;     // frame stride
@@ -406,11 +408,12 @@ __device__ __forceinline__ void carry_store(int *c, int64_t P, int64_t p, const 
     c[19 * P] = npend > 1 ? fs.ri[fs.slot(pj + 1)] : 0;
 }
 
-template <int ORDER, typename OutT, bool SEGMENTS, int MAXJ>
+template <int ORDER, typename OutT, bool SEGMENTS, int MAXJ, int TT>
 __global__ void __launch_bounds__(NTHREADS, 3)
     spk_scan_kernel(const __grid_constant__ Batch<MAXJ> prm) {
+    constexpr int WPT = TT / 32;  // 32-step words per tile
     extern __shared__ uint8_t smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+    Smem<TT> &sm = *reinterpret_cast<Smem<TT> *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
     __shared__ int s_job;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -484,14 +487,15 @@ __global__ void __launch_bounds__(NTHREADS, 3)
             ok = false;
             break;
         }
-        const uint32_t r0 = lds_u32(&sm.stage[s][lane][warp * 4]);
-        const uint32_t r1 = lds_u32(&sm.stage[s][lane + 32][warp * 4]);
+        uint32_t r[WPT];
+#pragma unroll
+        for (int h = 0; h < WPT; ++h) r[h] = lds_u32(&sm.stage[s][lane + 32 * h][warp * 4]);
         // each lane orders its own reads before the producer may refill this stage
         fence_proxy_async_smem();
         mbar_arrive(&sm.empty[s]);
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            uint32_t w = warp_transpose32(h ? r1 : r0, lane);
+#pragma unroll
+        for (int h = 0; h < WPT; ++h) {
+            uint32_t w = warp_transpose32(r[h], lane);
             if (!valid) w = 0;
             const int base = job.t_base + j * TT + h * 32;
             if (sc.last_t < 0 && w) {  // the stream's first spike opens the first sequence
@@ -582,6 +586,7 @@ struct spk_ctx {
     void *d_out;
     size_t out_cap;
     int64_t launches;
+    int tile;        // time tile of the frames kernels: 32, 64 or 128 steps
     char msg[512];
 };
 
@@ -640,12 +645,12 @@ int check_stream_args(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, 
     return SPK_OK;
 }
 
-int make_tmap(spk_ctx *ctx, CUtensorMap *map, const uint8_t *stream, int64_t pitch, int rows) {
+int make_tmap(spk_ctx *ctx, CUtensorMap *map, const uint8_t *stream, int64_t pitch, int rows, int tile) {
     auto enc = get_encode();
     if (!enc) return fail(ctx, SPK_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(pitch), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch)};
-    cuuint32_t box[2] = {ROW_BYTES, TT};
+    cuuint32_t box[2] = {ROW_BYTES, static_cast<cuuint32_t>(tile)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(stream), dims, strides, box,
                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -656,32 +661,50 @@ int make_tmap(spk_ctx *ctx, CUtensorMap *map, const uint8_t *stream, int64_t pit
 
 constexpr int MAXJ_BATCH = 96;  // jobs per launch (kernel parameters stay under 32 KB)
 
-template <int ORDER, typename OutT, bool SEG, int MAXJ>
+template <int ORDER, typename OutT, bool SEG, int MAXJ, int TT>
 int launch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
-    auto kern = spk_scan_kernel<ORDER, OutT, SEG, MAXJ>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
-        return fail(ctx, SPK_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(cudaGetLastError()));
-    kern<<<static_cast<unsigned>(nblocks), NTHREADS, SMEM_BYTES, ctx->stream>>>(prm);
+    auto kern = spk_scan_kernel<ORDER, OutT, SEG, MAXJ, TT>;
+    static bool attr_set[64];  // per device, once (the first launch should precede any graph capture)
+    const int dev = ctx->cfg.device;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<TT>()) != cudaSuccess)
+            return fail(ctx, SPK_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(cudaGetLastError()));
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    kern<<<static_cast<unsigned>(nblocks), NTHREADS, smem_bytes<TT>(), ctx->stream>>>(prm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
     ++ctx->launches;
     return SPK_OK;
 }
 
-template <int MAXJ>
-int dispatch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks, bool segments) {
+template <int MAXJ, int TT>
+int dispatch_tile(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
     const int order = ctx->cfg.order;
-    if (segments) return order == 1 ? launch<1, float, true>(ctx, prm, nblocks) : launch<2, float, true>(ctx, prm, nblocks);
     if (ctx->cfg.out_dtype == SPK_F16)
-        return order == 1 ? launch<1, __half, false>(ctx, prm, nblocks) : launch<2, __half, false>(ctx, prm, nblocks);
-    return order == 1 ? launch<1, float, false>(ctx, prm, nblocks) : launch<2, float, false>(ctx, prm, nblocks);
+        return order == 1 ? launch<1, __half, false, MAXJ, TT>(ctx, prm, nblocks)
+                          : launch<2, __half, false, MAXJ, TT>(ctx, prm, nblocks);
+    return order == 1 ? launch<1, float, false, MAXJ, TT>(ctx, prm, nblocks)
+                      : launch<2, float, false, MAXJ, TT>(ctx, prm, nblocks);
+}
+
+// frames kernels come in three time tiles (the autotuner's choice); the verification
+// kernel in the default tile only
+template <int MAXJ>
+int dispatch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks, bool segments, int tile) {
+    if (segments)
+        return ctx->cfg.order == 1 ? launch<1, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
+                                   : launch<2, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+    if (tile == 32) return dispatch_tile<MAXJ, 32>(ctx, prm, nblocks);
+    if (tile == 128) return dispatch_tile<MAXJ, 128>(ctx, prm, nblocks);
+    return dispatch_tile<MAXJ, 64>(ctx, prm, nblocks);
 }
 
 // one job's kernel parameters; returns its block count (or a negative error)
 int fill_job(spk_ctx *ctx, CUtensorMap *map, Job *job, const uint8_t *stream, int H, int W, int n, int t_base,
-             int T, float threshold, void *out, int *carry, int *ready, int flags, int block0) {
+             int T, float threshold, void *out, int *carry, int *ready, int flags, int block0, int tile) {
     const int64_t P = static_cast<int64_t>(H) * W;
-    int rc = make_tmap(ctx, map, stream, pitch_of(H, W), n);
+    int rc = make_tmap(ctx, map, stream, pitch_of(H, W), n, tile);
     if (rc) return rc;
     *job = Job{};
     job->P = P;
@@ -689,7 +712,7 @@ int fill_job(spk_ctx *ctx, CUtensorMap *map, Job *job, const uint8_t *stream, in
     job->carry = carry;
     job->ready = ready;
     job->n = n;
-    job->ntiles = (n + TT - 1) / TT;
+    job->ntiles = (n + tile - 1) / tile;
     job->t_base = t_base;
     job->stride = ctx->cfg.frame_stride;
     job->T_out = static_cast<int>((static_cast<int64_t>(T) + job->stride - 1) / job->stride);
@@ -711,8 +734,9 @@ int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float thr
              int32_t *counts, int32_t *ts, int32_t *te, int32_t *n, float *v, int cap, bool segments) {
     if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
     Batch<1> prm{};
+    const int tile = segments ? TT_DEFAULT : ctx->tile;
     const int nb = fill_job(ctx, &prm.maps[0], &prm.jobs[0], stream, H, W, T, 0, T, threshold, out, nullptr,
-                            nullptr, JOB_FIRST | JOB_LAST, 0);
+                            nullptr, JOB_FIRST | JOB_LAST, 0, tile);
     if (nb < 0) return nb;
     prm.njobs = 1;
     prm.status = ctx->d_status;
@@ -722,7 +746,7 @@ int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float thr
     prm.seg_n = n;
     prm.seg_v = v;
     prm.cap = cap;
-    return dispatch(ctx, prm, nb, segments);
+    return dispatch(ctx, prm, nb, segments, tile);
 }
 
 bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
@@ -759,6 +783,7 @@ int spk_create(spk_ctx **out, const spk_config *cfg) {
     if (!c) return fail(nullptr, SPK_ERR_OOM, "host allocation failed");
     c->cfg = *cfg;
     c->stream = static_cast<cudaStream_t>(cfg->stream);
+    c->tile = TT_DEFAULT;
     if (cudaMalloc(&c->d_status, 16) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -921,13 +946,29 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
     }
     if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
     Batch<MAXJ_BATCH> *prm = new (std::nothrow) Batch<MAXJ_BATCH>();
-    if (!prm) return fail(ctx, SPK_ERR_OOM, "host allocation failed");
+    int *order = static_cast<int *>(malloc(sizeof(int) * (njobs > 0 ? njobs : 1)));
+    if (!prm || !order) {
+        delete prm;
+        free(order);
+        return fail(ctx, SPK_ERR_OOM, "host allocation failed");
+    }
+    // longest pieces first: their blocks take longest, so they should start first
+    for (int k = 0; k < njobs; ++k) order[k] = k;
+    for (int k = 1; k < njobs; ++k) {
+        const int x = order[k];
+        int m = k;
+        while (m > 0 && jobs[order[m - 1]].n < jobs[x].n) {
+            order[m] = order[m - 1];
+            --m;
+        }
+        order[m] = x;
+    }
     int rc = SPK_OK;
     for (int k0 = 0; k0 < njobs && rc == SPK_OK; k0 += MAXJ_BATCH) {
         const int nj = njobs - k0 < MAXJ_BATCH ? njobs - k0 : MAXJ_BATCH;
         int blocks = 0;
         for (int k = 0; k < nj && rc == SPK_OK; ++k) {
-            const spk_job &jb = jobs[k0 + k];
+            const spk_job &jb = jobs[order[k0 + k]];
             spk_stream *st = jb.state;
             int flags = JOB_FIRST | JOB_LAST, t_base = 0, T = jb.n;
             if (st) {
@@ -939,19 +980,64 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
             }
             const int nb = fill_job(ctx, &prm->maps[k], &prm->jobs[k], jb.stream, jb.H, jb.W, jb.n, t_base, T,
                                     jb.threshold, jb.out_frames, st ? st->d_carry : nullptr,
-                                    st ? st->d_ready : nullptr, flags, blocks);
+                                    st ? st->d_ready : nullptr, flags, blocks, ctx->tile);
             if (nb < 0) rc = nb;
             else blocks += nb;
         }
         if (rc) break;
         prm->njobs = nj;
         prm->status = ctx->d_status;
-        rc = dispatch(ctx, *prm, blocks, false);
+        rc = dispatch(ctx, *prm, blocks, false, ctx->tile);
         if (rc == SPK_OK)
             for (int k = 0; k < nj; ++k)
-                if (jobs[k0 + k].state) jobs[k0 + k].state->pushed += jobs[k0 + k].n;
+                if (jobs[order[k0 + k]].state) jobs[order[k0 + k]].state->pushed += jobs[order[k0 + k]].n;
     }
     delete prm;
+    free(order);
+    return rc;
+}
+
+int spk_set_tile(spk_ctx *ctx, int tile) {
+    if (!ctx) return SPK_ERR_ARG;
+    if (tile != 32 && tile != 64 && tile != 128) return fail(ctx, SPK_ERR_ARG, "tile must be 32, 64 or 128");
+    ctx->tile = tile;
+    return SPK_OK;
+}
+
+int spk_get_tile(const spk_ctx *ctx) { return ctx ? ctx->tile : -1; }
+
+int spk_autotune(spk_ctx *ctx, const spk_job *jobs, int njobs, int *best_tile) {
+    if (!ctx) return SPK_ERR_ARG;
+    ctx->msg[0] = 0;
+    for (int k = 0; k < njobs; ++k)
+        if (jobs[k].state) return fail(ctx, SPK_ERR_ARG, "autotune runs jobs repeatedly: whole streams only");
+    cudaSetDevice(ctx->cfg.device);
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "cudaEventCreate failed");
+    const int tiles[3] = {32, 64, 128};
+    float best_ms = -1.f;
+    int best = ctx->tile, rc = SPK_OK;
+    for (int m = 0; m < 3 && rc == SPK_OK; ++m) {
+        ctx->tile = tiles[m];
+        rc = spk_run(ctx, jobs, njobs);  // warm-up
+        if (rc) break;
+        cudaEventRecord(a, ctx->stream);
+        for (int r = 0; r < 3 && rc == SPK_OK; ++r) rc = spk_run(ctx, jobs, njobs);
+        cudaEventRecord(b, ctx->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) rc = fail(ctx, SPK_ERR_CUDA, "autotune run failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rc == SPK_OK && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best = tiles[m];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->tile = best;
+    if (best_tile) *best_tile = best;
+    if (rc == SPK_OK) rc = spk_synchronize(ctx);
     return rc;
 }
 
@@ -1079,10 +1165,11 @@ extern "C" int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t
 
     spk_ctx tmp{};  // host-side view for the shared launch path; owns no device memory
     tmp.cfg = *cfg;
+    tmp.tile = TT_DEFAULT;
     tmp.stream = static_cast<cudaStream_t>(cfg->stream);
     tmp.d_status = d_status;
     auto bail = [&](int code) {
-        snprintf(g_create_msg, sizeof(g_create_msg), "%s", tmp.msg);
+        snprintf(g_create_msg, sizeof(g_create_msg), "%.480s", tmp.msg);
         return code;
     };
     // the array keeps the previous call's contents: clear the status word first

@@ -18,7 +18,8 @@ _c = ctypes
 EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
            "spk_reconstruct_host", "spk_segments", "spk_synchronize", "spk_last_error",
            "spk_launch_count", "spk_reconstruct_host_noalloc", "spk_selftest_wait", "spk_stream_open",
-           "spk_stream_close", "spk_stream_steps", "spk_stream_ready", "spk_run")
+           "spk_stream_close", "spk_stream_steps", "spk_stream_ready", "spk_run", "spk_set_tile",
+           "spk_get_tile", "spk_autotune")
 SPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -81,6 +82,12 @@ def load(path: str | None = None):
     lib.spk_stream_ready.restype = i32
     lib.spk_run.argtypes = [vp, _c.POINTER(spk_job), i32]
     lib.spk_run.restype = i32
+    lib.spk_set_tile.argtypes = [vp, i32]
+    lib.spk_set_tile.restype = i32
+    lib.spk_get_tile.argtypes = [vp]
+    lib.spk_get_tile.restype = i32
+    lib.spk_autotune.argtypes = [vp, _c.POINTER(spk_job), i32, _c.POINTER(i32)]
+    lib.spk_autotune.restype = i32
     lib.spk_selftest_wait.argtypes = [vp, i64]
     lib.spk_selftest_wait.restype = i32
     lib.spk_reconstruct_host_noalloc.argtypes = [_c.POINTER(spk_config), vp, i32, i32, i32, f32, vp]
@@ -193,9 +200,27 @@ def spk_stream_ready(ctx, state) -> int:
     return r.value
 
 
-def spk_run(ctx, jobs):
-    """jobs: sequence of (stream, H, W, n, threshold, out_frames, state_or_None)."""
-    arr = (spk_job * len(jobs))()
+def _jobs(jobs):
+    arr = (spk_job * max(len(jobs), 1))()
     for k, (st, H, W, n, th, out, state) in enumerate(jobs):
         arr[k] = spk_job(_addr(st), H, W, n, th, _addr(out), state)
-    return _check(ctx, load().spk_run(ctx, arr, len(jobs)))
+    return arr
+
+
+def spk_run(ctx, jobs):
+    """jobs: sequence of (stream, H, W, n, threshold, out_frames, state_or_None)."""
+    return _check(ctx, load().spk_run(ctx, _jobs(jobs), len(jobs)))
+
+
+def spk_set_tile(ctx, tile: int):
+    return _check(ctx, load().spk_set_tile(ctx, tile))
+
+
+def spk_get_tile(ctx) -> int:
+    return load().spk_get_tile(ctx)
+
+
+def spk_autotune(ctx, jobs) -> int:
+    best = _c.c_int()
+    _check(ctx, load().spk_autotune(ctx, _jobs(jobs), len(jobs), _c.byref(best)))
+    return best.value

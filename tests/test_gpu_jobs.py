@@ -152,3 +152,42 @@ def test_job_argument_errors(env):
     assert S.ready() == 100
     S.close()
     R.close()
+
+
+def test_batch_captured_in_cuda_graph_and_autotuned(env):
+    """A batch of whole streams captured once in a CUDA graph and replayed gives the same
+    frames; the autotuner picks one of the tiles and every tile gives identical frames."""
+    torch, pkg = env
+    from paper_2412_11639_gb300 import spk
+    rng = np.random.default_rng(9)
+    side = torch.cuda.Stream()
+    R = pkg.Reconstructor(order=2, stride=5, stream=side)
+    jobs, outs, refs = [], [], []
+    for k in range(10):
+        H, W, T = int(rng.integers(4, 40)), int(rng.integers(8, 80)), int(rng.integers(100, 3000))
+        st = _stream("dynamic_250x400x20000" if k % 2 else "random", H, W, T, k)
+        d = torch.from_numpy(st).cuda()
+        o = R.alloc_frames(H, W, T)
+        jobs.append((d, H, W, T, 1.0, o, None))
+        outs.append(o)
+        refs.append(_whole(env, st, H, W, T, 2, 5, torch.float32))
+    best = spk.spk_autotune(R.ctx, jobs)
+    assert best in (32, 64, 128) and spk.spk_get_tile(R.ctx) == best
+    for tile in (32, 64, 128):
+        spk.spk_set_tile(R.ctx, tile)
+        with torch.cuda.stream(side):
+            pkg.spk_run(R.ctx, jobs)                 # also sets the kernel attributes
+        torch.cuda.synchronize()
+        for o, ref in zip(outs, refs):
+            assert np.array_equal(o.cpu().numpy().view(np.uint32), ref.view(np.uint32)), tile
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            pkg.spk_run(R.ctx, jobs)
+        for o in outs:                             # capture does not run the kernel
+            o.fill_(-1.0)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        for o, ref in zip(outs, refs):
+            assert np.array_equal(o.cpu().numpy().view(np.uint32), ref.view(np.uint32)), tile
+    R.close()
