@@ -42,7 +42,9 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dynamic_250x400x20000")
-    ap.add_argument("--order", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3, 4],
+                    help="method: 1 FSR, 2 SSR (default), 3 TFI, 4 TFP (window --tfp-window)")
+    ap.add_argument("--tfp-window", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["single", "batch", "serve"], default="single",
@@ -190,11 +192,16 @@ def recorded_traffic(workload: str, order: int):
 
 
 # ------------------------------------------------------------------ CPU oracle ----
-def oracle_rate(st, w, order, pixels=None):
+def oracle_rate(st, w, order, pixels=None, window=32):
     """Gpixel-frames/s of the fp64 CPU oracle over the given pixels (all by default)."""
     import oracle
     t0 = time.perf_counter()
-    r = oracle.reconstruct(st, w.H, w.W, w.T, 1.0, order, w.stride, pixels=pixels, frames=True)
+    if order == 3:
+        r = oracle.tfi(st, w.H, w.W, w.T, 1.0, w.stride, pixels=pixels)
+    elif order == 4:
+        r = oracle.tfp(st, w.H, w.W, w.T, window, 1.0, w.stride, pixels=pixels)
+    else:
+        r = oracle.reconstruct(st, w.H, w.W, w.T, 1.0, order, w.stride, pixels=pixels, frames=True)
     dt = time.perf_counter() - t0
     npix = w.P if pixels is None else len(pixels)
     del r
@@ -244,9 +251,13 @@ def run_reference(args, rank, world):
     return 0
 
 
-def config_of(w, order):
+METHODS = {1: "FSR", 2: "SSR", 3: "TFI", 4: "TFP"}
+
+
+def config_of(w, order, window=32):
+    name = METHODS[order] + (f"-{window}" if order == 4 else "")
     return {"workload": w.name, "H": w.H, "W": w.W, "T": w.T, "frame_stride": w.stride,
-            "T_out": w.T_out, "out_dtype": w.out_dtype, "method": "SSR" if order == 2 else "FSR",
+            "T_out": w.T_out, "out_dtype": w.out_dtype, "method": name,
             "threshold": 1.0, "parallelism": "replicas, one per GPU",
             "l2": "inputs and outputs larger than the 129 MB L2 (no flush)"}
 
@@ -262,7 +273,8 @@ def run_ours(args, rank, world, local_rank):
     w, st = workload_stream(args.workload, rank, world)
     dtype = torch.float16 if w.out_dtype == "f16" else torch.float32
     esz = 2 if dtype == torch.float16 else 4
-    R = pkg.Reconstructor(order=args.order, stride=w.stride, dtype=dtype, device=local_rank)
+    R = pkg.Reconstructor(order=args.order, stride=w.stride, dtype=dtype, device=local_rank,
+                          tfp_window=args.tfp_window)
     dev = torch.from_numpy(st).cuda()
     out = R.alloc_frames(w.H, w.W, w.T)
     stream = R.stream
@@ -319,7 +331,7 @@ def run_ours(args, rank, world, local_rank):
         return 0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt, npix = oracle_rate(st, w, args.order)
+        v, dt, npix = oracle_rate(st, w, args.order, window=args.tfp_window)
         cpu = {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"the whole workload once ({npix} pixels x {w.T_out} frames, {dt:.1f} s)"}
     traffic = recorded_traffic(w.name, args.order)
@@ -327,7 +339,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic",
-        "config": config_of(w, args.order),
+        "config": config_of(w, args.order, args.tfp_window),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",

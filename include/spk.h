@@ -52,13 +52,22 @@ enum spk_status {
 
 enum spk_dtype { SPK_F32 = 0, SPK_F16 = 1 };
 
+/* Reconstruction methods.  FSR and SSR are the paper's (Sec. III-B); TFI and TFP are the
+ * physical-model baselines it compares them with (Sec. II, Tables II-III):
+ *  SPK_TFI: theta / the interval (s_i, s_{i+1}] covering t_k (every interval is its own
+ *           span, with the frame policy above);
+ *  SPK_TFP: theta * (spikes in the tfp_window steps (t_k - L, t_k]) / L, steps before the
+ *           stream counting as empty; whole streams only (no spk_stream, no spk_segments). */
+enum spk_method { SPK_FSR = 1, SPK_SSR = 2, SPK_TFI = 3, SPK_TFP = 4 };
+
 typedef struct spk_config {
-    int order;          /* 1 = FSR, 2 = SSR */
+    int method;         /* SPK_FSR, SPK_SSR, SPK_TFI or SPK_TFP */
     int frame_stride;   /* >= 1: frame k samples step k * frame_stride */
     int out_dtype;      /* SPK_F32 or SPK_F16 (fp16 is the round-to-nearest-even of the
                            fp32 value) */
     int device;         /* CUDA device ordinal */
     void *stream;       /* cudaStream_t to launch on; NULL = the legacy default stream */
+    int tfp_window;     /* SPK_TFP only: window L in steps, 1..64 (the paper uses 32, 64) */
 } spk_config;
 
 typedef struct spk_ctx spk_ctx;
@@ -101,7 +110,8 @@ int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W,
  * same state across its 32-frame chunks. */
 typedef struct spk_stream spk_stream;
 
-/* Opens a stream of H x W pixels and T steps on ctx (its order, frame stride, output type)
+/* Opens a stream of H x W pixels and T steps on ctx (its method -- FSR, SSR or TFI --,
+ * frame stride and output type)
  * and allocates its device state: 20 int32 per pixel (the stability scan, the frames
  * already written, the cut that opens the current span, up to two pending cut
  * candidates) and one int32.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM. */
@@ -200,7 +210,8 @@ int spk_selftest_wait(spk_ctx *ctx, int64_t limit_cycles);
  * device it is loaded on, until the process exits.  It calls no cudaMalloc, cudaFree or
  * allocating library routine.
  *
- *   cfg           order, frame_stride, out_dtype, device and stream, as for spk_create
+ *   cfg           method, frame_stride, out_dtype, device, stream, tfp_window, as for
+ *                 spk_create
  *                 (the stream must belong to cfg->device)
  *   host_stream   host, uint8 [T][spk_pitch(H, W)]
  *   host_frames   host, [T_out][H][W] of cfg->out_dtype, written completely

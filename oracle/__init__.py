@@ -42,6 +42,12 @@ def _load():
         lib.oracle_reconstruct.restype = c.c_int
         lib.oracle_spike_times.argtypes = [c.c_void_p, c.c_int64, c.c_int, c.c_int64, c.c_void_p]
         lib.oracle_spike_times.restype = c.c_int
+        lib.oracle_tfi.argtypes = [c.c_void_p, c.c_int64, c.c_int64, c.c_int, c.c_double, c.c_int,
+                                   c.c_void_p, c.c_int64, c.c_void_p]
+        lib.oracle_tfi.restype = c.c_int
+        lib.oracle_tfp.argtypes = [c.c_void_p, c.c_int64, c.c_int64, c.c_int, c.c_double, c.c_int,
+                                   c.c_int, c.c_void_p, c.c_int64, c.c_void_p]
+        lib.oracle_tfp.restype = c.c_int
         _lib = lib
     return _lib
 
@@ -117,3 +123,31 @@ def reconstruct(stream: np.ndarray, H: int, W: int, T: int, theta: float = 1.0, 
         if rc != 0:
             raise ValueError(f"oracle_reconstruct (segments) failed ({rc})")
     return r
+
+
+def tfi(stream: np.ndarray, H: int, W: int, T: int, theta: float = 1.0, stride: int = 1,
+        pixels=None) -> np.ndarray:
+    """TFI baseline (Sec. II): frames fp64 [T_out][npix]."""
+    stream = np.ascontiguousarray(stream, dtype=np.uint8)
+    pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
+    npix = H * W if pix is None else pix.shape[0]
+    out = np.empty(((T + stride - 1) // stride, npix), dtype=np.float64)
+    rc = _load().oracle_tfi(stream.ctypes.data, stream.shape[1], H * W, T, theta, stride, _ptr(pix),
+                            npix, out.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_tfi failed ({rc})")
+    return out
+
+
+def tfp(stream: np.ndarray, H: int, W: int, T: int, window: int, theta: float = 1.0,
+        stride: int = 1, pixels=None) -> np.ndarray:
+    """TFP baseline (Sec. II) with a window of `window` steps: frames fp64 [T_out][npix]."""
+    stream = np.ascontiguousarray(stream, dtype=np.uint8)
+    pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
+    npix = H * W if pix is None else pix.shape[0]
+    out = np.empty(((T + stride - 1) // stride, npix), dtype=np.float64)
+    rc = _load().oracle_tfp(stream.ctypes.data, stream.shape[1], H * W, T, theta, stride, window,
+                            _ptr(pix), npix, out.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_tfp failed ({rc})")
+    return out

@@ -93,3 +93,28 @@ def frames(bits, order: int = 1, stride: int = 1, theta=1):
             continue
         out.append(next(v for (ts, te, _n, v) in segs if ts < t <= te))
     return out
+
+
+def tfi_frames(bits, stride: int = 1, theta=1):
+    """TFI (Sec. II): theta over the interval between the two adjacent spikes around t_k."""
+    s = spike_times(bits)
+    T = len(bits)
+    out = []
+    for k in range((T + stride - 1) // stride):
+        t = k * stride
+        if len(s) < 2:
+            out.append(Fraction(0))
+            continue
+        # the interval (s_j, s_j+1] holding t; clamp to the first / last interval
+        j = next((j for j in range(len(s) - 1) if s[j] < t <= s[j + 1]), None)
+        if j is None:
+            j = 0 if t <= s[0] else len(s) - 2
+        out.append(Fraction(theta) / (s[j + 1] - s[j]))
+    return out
+
+
+def tfp_frames(bits, window: int, stride: int = 1, theta=1):
+    """TFP (Sec. II): theta * spikes in the `window` steps ending at t_k / window."""
+    T = len(bits)
+    return [Fraction(theta) * sum(bits[u] for u in range(max(0, k * stride - window + 1), k * stride + 1))
+            / window for k in range((T + stride - 1) // stride)]

@@ -215,3 +215,76 @@ int oracle_reconstruct(const uint8_t *stream, int64_t pitch, int64_t P, int T, d
     }
     return err;
 }
+
+/*
+ * Baselines of Sec. II (the paper compares FSR/SSR with them, Tables II-III).
+ *
+ * TFI (texture from inter-spike interval): the intensity is theta divided by the interval
+ * between two adjacent spikes.  Frame k takes the interval (s_i, s_{i+1}] covering
+ * t_k = k * stride; before the first spike the first interval, after the last spike the
+ * last interval, fewer than two spikes 0 (the frame policy of the FSR/SSR frames).
+ *
+ * TFP (texture from playback): a virtual exposure window of L steps; the intensity is
+ * theta * N_spk / L, N_spk the spikes in the window.  Frame k's window is the L steps
+ * ending at t_k, (t_k - L, t_k]; steps before the stream count as empty.
+ *
+ * frames [T_out][npix] fp64 as in oracle_reconstruct; pix == NULL means all pixels.
+ */
+int oracle_tfi(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta, int stride,
+               const int64_t *pix, int64_t npix, double *frames) {
+    if (P <= 0 || T <= 0 || pitch * 8 < P || stride <= 0) return -1;
+    if (pix == NULL) npix = P;
+    int T_out = (T + stride - 1) / stride;
+    int err = 0;
+#pragma omp parallel
+    {
+        int32_t *s = (int32_t *)malloc(sizeof(int32_t) * (size_t)T);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < npix; ++i) {
+            int64_t p = pix ? pix[i] : i;
+            if (p < 0 || p >= P) {
+#pragma omp atomic write
+                err = -1;
+                continue;
+            }
+            int K = oracle_spike_times(stream, pitch, T, p, s);
+            int j = 0;  /* interval j = (s_j, s_{j+1}] */
+            for (int k = 0; k < T_out; ++k) {
+                int64_t t = (int64_t)k * stride;
+                double v = 0.0;
+                if (K >= 2) {
+                    while (j < K - 2 && t > s[j + 1]) ++j;
+                    v = theta / (double)(s[j + 1] - s[j]);
+                }
+                frames[(int64_t)k * npix + i] = v;
+            }
+        }
+        free(s);
+    }
+    return err;
+}
+
+int oracle_tfp(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta, int stride, int L,
+               const int64_t *pix, int64_t npix, double *frames) {
+    if (P <= 0 || T <= 0 || pitch * 8 < P || stride <= 0 || L <= 0) return -1;
+    if (pix == NULL) npix = P;
+    int T_out = (T + stride - 1) / stride;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < npix; ++i) {
+        int64_t p = pix ? pix[i] : i;
+        if (p < 0 || p >= P) {
+#pragma omp atomic write
+            err = -1;
+            continue;
+        }
+        for (int k = 0; k < T_out; ++k) {
+            int64_t t = (int64_t)k * stride;
+            int n = 0;
+            for (int64_t u = t - L + 1; u <= t; ++u)
+                if (u >= 0 && u < T && spike_bit(stream, pitch, (int)u, p)) ++n;
+            frames[(int64_t)k * npix + i] = theta * (double)n / (double)L;
+        }
+    }
+    return err;
+}

@@ -23,12 +23,13 @@ __all__ = ["spk", "build", "Reconstructor", "SpkError", "SPK_F32", "SPK_F16", "s
 class Reconstructor:
     """One libspk context bound to a torch CUDA stream.
 
-    order 1 = FSR, 2 = SSR; frame k samples step k * stride; dtype torch.float32 or
-    torch.float16.  Device memory comes from torch; the reconstruction runs in libspk.
+    order (the method): 1 = FSR, 2 = SSR, 3 = TFI, 4 = TFP (window tfp_window steps);
+    frame k samples step k * stride; dtype torch.float32 or torch.float16.  Device memory
+    comes from torch; the reconstruction runs in libspk.
     """
 
     def __init__(self, order: int = 2, stride: int = 1, dtype=None, device: int = 0,
-                 stream=None):
+                 stream=None, tfp_window: int = 32):
         import torch
         self.torch = torch
         dtype = dtype or torch.float32
@@ -38,7 +39,7 @@ class Reconstructor:
         self.order, self.stride, self.device = order, stride, device
         self.stream = stream or torch.cuda.current_stream(device)
         self.ctx = spk_create(order, stride, SPK_F16 if dtype == torch.float16 else SPK_F32,
-                              device, self.stream.cuda_stream)
+                              device, self.stream.cuda_stream, tfp_window)
 
     def close(self):
         if self.ctx is not None:

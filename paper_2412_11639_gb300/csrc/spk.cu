@@ -80,6 +80,7 @@ struct Job {
     uint32_t div_m; // t / stride = umulhi(t, div_m) >> div_s for 0 <= t < 2^31 (stride >= 2)
     int div_s;
     float theta;    // threshold of Eq. 4
+    int window;     // TFP window in steps
     int flags;      // JOB_FIRST | JOB_LAST
     int block0;     // first block of this job in the flat grid
 };
@@ -553,6 +554,92 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     }
 }
 
+// ------------------------------------------------------------------ TFP kernel ----
+// TFP (Sec. II): frame k = theta * (spikes in the L steps (t_k - L, t_k]) / L.  The same
+// TMA pipeline and transpose feed one lane per pixel; a frame needs no future, so every
+// frame row is written (coalesced) as soon as the scan passes its sampling step.
+template <int TT>
+struct StageSmem {
+    uint8_t stage[NS][TT][ROW_BYTES];
+    unsigned long long full[NS];
+    unsigned long long empty[NS];
+};
+
+template <typename OutT, int MAXJ, int TT>
+__global__ void __launch_bounds__(NTHREADS, 3) spk_tfp_kernel(const __grid_constant__ Batch<MAXJ> prm) {
+    constexpr int WPT = TT / 32;
+    extern __shared__ uint8_t smem_raw[];
+    StageSmem<TT> &sm = *reinterpret_cast<StageSmem<TT> *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+    __shared__ int s_job;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        int jb = 0;
+        for (int k = 1; k < prm.njobs; ++k)
+            if (static_cast<int>(blockIdx.x) >= prm.jobs[k].block0) jb = k;
+        s_job = jb;
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NCW * 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int jb = s_job;
+    const Job &job = prm.jobs[jb];
+    const int blk = static_cast<int>(blockIdx.x) - job.block0;
+    if (warp == NCW) {  // producer warp: as in the scan kernel
+        if (lane == 0) {
+            const CUtensorMap *map = &prm.maps[jb];
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+            int issued = 0;
+            for (int j = 0; j < job.ntiles; ++j) {
+                const int s = j % NS;
+                if (j >= NS && !mbar_wait(&sm.empty[s], ((j / NS) - 1) & 1, prm.status)) break;
+                mbar_arrive_expect_tx(&sm.full[s], TT * ROW_BYTES);
+                tma_load_2d(&sm.stage[s][0][0], map, &sm.full[s], blk * ROW_BYTES, j * TT);
+                issued = j + 1;
+            }
+            for (int j = issued > NS ? issued - NS : 0; j < issued; ++j)
+                if (!mbar_wait(&sm.full[j % NS], (j / NS) & 1, prm.status)) break;
+        }
+        return;
+    }
+    const int64_t p = static_cast<int64_t>(blk) * BLOCK_PIX + warp * 32 + lane;
+    const bool valid = p < job.P;
+    OutT *col = static_cast<OutT *>(job.out) + (valid ? p : 0);
+    const int L = job.window;
+    uint32_t h1 = 0, h2 = 0;  // the two previous words (steps before the stream are empty)
+    int k = 0;                // next frame
+    for (int j = 0; j < job.ntiles; ++j) {
+        const int s = j % NS;
+        if (!__all_sync(FULL, mbar_wait(&sm.full[s], (j / NS) & 1, prm.status))) return;
+        uint32_t r[WPT];
+#pragma unroll
+        for (int h = 0; h < WPT; ++h) r[h] = lds_u32(&sm.stage[s][lane + 32 * h][warp * 4]);
+        fence_proxy_async_smem();
+        mbar_arrive(&sm.empty[s]);
+#pragma unroll
+        for (int h = 0; h < WPT; ++h) {
+            uint32_t w = warp_transpose32(r[h], lane);
+            if (!valid) w = 0;
+            const int base = job.t_base + j * TT + h * 32;
+            const unsigned long long hist = static_cast<unsigned long long>(h2) |
+                                            (static_cast<unsigned long long>(h1) << 32);
+            for (; k < job.T_out && k * job.stride < base + 32; ++k) {  // frames sampled in this word
+                const int o = k * job.stride - base;
+                const int lo = o - L + 1;
+                const uint32_t upto = (2u << o) - 1u;  // bits 0..o
+                int cnt = __popc(w & upto & ~((1u << (lo > 0 ? lo : 0)) - 1u));
+                if (lo < 0) cnt += __popcll(hist >> (64 + lo));  // the -lo steps before this word
+                if (valid) col[static_cast<int64_t>(k) * job.P] =
+                    to_out<OutT>(__fdiv_rn(__fmul_rn(job.theta, static_cast<float>(cnt)), static_cast<float>(L)));
+            }
+            h2 = h1;
+            h1 = w;
+        }
+    }
+}
+
 // Self-test of the bounded waits: one warp waits on an mbarrier that nothing arrives at,
 // through the same mbar_wait the scan uses, gives up after `limit` cycles and flags the
 // status word.
@@ -678,26 +765,56 @@ int launch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
     return SPK_OK;
 }
 
-template <int MAXJ, int TT>
-int dispatch_tile(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
-    const int order = ctx->cfg.order;
-    if (ctx->cfg.out_dtype == SPK_F16)
-        return order == 1 ? launch<1, __half, false, MAXJ, TT>(ctx, prm, nblocks)
-                          : launch<2, __half, false, MAXJ, TT>(ctx, prm, nblocks);
-    return order == 1 ? launch<1, float, false, MAXJ, TT>(ctx, prm, nblocks)
-                      : launch<2, float, false, MAXJ, TT>(ctx, prm, nblocks);
+template <typename OutT, int MAXJ>
+int launch_tfp(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
+    auto kern = spk_tfp_kernel<OutT, MAXJ, TT_DEFAULT>;
+    constexpr size_t bytes = sizeof(StageSmem<TT_DEFAULT>) + 128;
+    kern<<<static_cast<unsigned>(nblocks), NTHREADS, bytes, ctx->stream>>>(prm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    ++ctx->launches;
+    return SPK_OK;
 }
 
-// frames kernels come in three time tiles (the autotuner's choice); the verification
-// kernel in the default tile only
+template <int MAXJ, int TT>
+int dispatch_tile(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
+    const int m = ctx->cfg.method;
+    if (ctx->cfg.out_dtype == SPK_F16)
+        return m == SPK_FSR ? launch<1, __half, false, MAXJ, TT>(ctx, prm, nblocks)
+                            : launch<2, __half, false, MAXJ, TT>(ctx, prm, nblocks);
+    return m == SPK_FSR ? launch<1, float, false, MAXJ, TT>(ctx, prm, nblocks)
+                        : launch<2, float, false, MAXJ, TT>(ctx, prm, nblocks);
+}
+
+// FSR / SSR frames kernels come in three time tiles (the autotuner's choice); TFI, TFP
+// and the verification kernel in the default tile only
 template <int MAXJ>
 int dispatch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks, bool segments, int tile) {
+    const int m = ctx->cfg.method;
+    const bool f16 = ctx->cfg.out_dtype == SPK_F16;
     if (segments)
-        return ctx->cfg.order == 1 ? launch<1, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
-                                   : launch<2, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+        return m == SPK_FSR ? launch<1, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
+             : m == SPK_TFI ? launch<3, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
+                            : launch<2, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+    if (m == SPK_TFI)
+        return f16 ? launch<3, __half, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
+                   : launch<3, float, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+    if (m == SPK_TFP)
+        return f16 ? launch_tfp<__half, MAXJ>(ctx, prm, nblocks) : launch_tfp<float, MAXJ>(ctx, prm, nblocks);
     if (tile == 32) return dispatch_tile<MAXJ, 32>(ctx, prm, nblocks);
     if (tile == 128) return dispatch_tile<MAXJ, 128>(ctx, prm, nblocks);
     return dispatch_tile<MAXJ, 64>(ctx, prm, nblocks);
+}
+
+// the tile a call will use: the context's for FSR / SSR, the default for the others
+int tile_of(const spk_ctx *ctx, bool segments) {
+    const int m = ctx->cfg.method;
+    return (segments || m == SPK_TFI || m == SPK_TFP) ? TT_DEFAULT : ctx->tile;
+}
+
+bool valid_method(const spk_config *cfg) {
+    if (cfg->method < SPK_FSR || cfg->method > SPK_TFP) return false;
+    return cfg->method != SPK_TFP || (cfg->tfp_window >= 1 && cfg->tfp_window <= 64);
 }
 
 // one job's kernel parameters; returns its block count (or a negative error)
@@ -725,6 +842,7 @@ int fill_job(spk_ctx *ctx, CUtensorMap *map, Job *job, const uint8_t *stream, in
         job->div_s = l - 1;
     }
     job->theta = threshold;
+    job->window = ctx->cfg.tfp_window;
     job->flags = flags;
     job->block0 = block0;
     return static_cast<int>((P + BLOCK_PIX - 1) / BLOCK_PIX);
@@ -734,7 +852,7 @@ int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float thr
              int32_t *counts, int32_t *ts, int32_t *te, int32_t *n, float *v, int cap, bool segments) {
     if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
     Batch<1> prm{};
-    const int tile = segments ? TT_DEFAULT : ctx->tile;
+    const int tile = tile_of(ctx, segments);
     const int nb = fill_job(ctx, &prm.maps[0], &prm.jobs[0], stream, H, W, T, 0, T, threshold, out, nullptr,
                             nullptr, JOB_FIRST | JOB_LAST, 0, tile);
     if (nb < 0) return nb;
@@ -769,7 +887,7 @@ int spk_create(spk_ctx **out, const spk_config *cfg) {
     if (!out) return fail(nullptr, SPK_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!cfg) return fail(nullptr, SPK_ERR_ARG, "cfg is NULL");
-    if (cfg->order != 1 && cfg->order != 2) return fail(nullptr, SPK_ERR_ARG, "order must be 1 or 2");
+    if (!valid_method(cfg)) return fail(nullptr, SPK_ERR_ARG, "method must be 1..4 (TFP: tfp_window 1..64)");
     if (cfg->frame_stride < 1) return fail(nullptr, SPK_ERR_ARG, "frame_stride must be >= 1");
     if (cfg->out_dtype != SPK_F32 && cfg->out_dtype != SPK_F16) return fail(nullptr, SPK_ERR_ARG, "bad out_dtype");
     int ndev = 0;
@@ -836,6 +954,7 @@ int spk_segments(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float
     int rc = check_stream_args(ctx, stream, H, W, T, threshold);
     if (rc) return rc;
     ctx->msg[0] = 0;
+    if (ctx->cfg.method == SPK_TFP) return fail(ctx, SPK_ERR_ARG, "TFP has no stable spans");
     if (!counts || cap < 0) return fail(ctx, SPK_ERR_ARG, "counts is NULL or cap < 0");
     if (cap > 0 && (!t_start || !t_end || !n_int || !value)) return fail(ctx, SPK_ERR_ARG, "segment arrays are NULL");
     if (!is_device_ptr(stream) || !is_device_ptr(counts)) return fail(ctx, SPK_ERR_ARG, "pointers must be device memory");
@@ -865,6 +984,7 @@ int spk_stream_open(spk_ctx *ctx, int H, int W, int T, spk_stream **out) {
     ctx->msg[0] = 0;
     if (!out) return fail(ctx, SPK_ERR_ARG, "out is NULL");
     *out = nullptr;
+    if (ctx->cfg.method == SPK_TFP) return fail(ctx, SPK_ERR_ARG, "TFP runs whole streams only");
     if (H <= 0 || W <= 0 || T <= 0 || T > (1 << 30)) return fail(ctx, SPK_ERR_ARG, "bad H, W or T");
     if (static_cast<int64_t>(H) * W > (1LL << 31) - BLOCK_PIX) return fail(ctx, SPK_ERR_ARG, "H*W too large");
     if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
@@ -937,6 +1057,7 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
         if (!is_device_ptr(jb.stream) || !is_device_ptr(jb.out_frames))
             return fail(ctx, SPK_ERR_ARG, "job %d: stream and out_frames must be device memory", k);
         if (jb.state) {
+            if (ctx->cfg.method == SPK_TFP) return fail(ctx, SPK_ERR_ARG, "TFP runs whole streams only");
             if (jb.state->H != jb.H || jb.state->W != jb.W) return fail(ctx, SPK_ERR_ARG, "job %d: H, W differ from its stream", k);
             if (jb.state->pushed + jb.n > jb.state->T) return fail(ctx, SPK_ERR_ARG, "job %d: piece runs past the stream's T", k);
             if (jb.state->device != ctx->cfg.device) return fail(ctx, SPK_ERR_ARG, "job %d: stream on another device", k);
@@ -980,14 +1101,14 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
             }
             const int nb = fill_job(ctx, &prm->maps[k], &prm->jobs[k], jb.stream, jb.H, jb.W, jb.n, t_base, T,
                                     jb.threshold, jb.out_frames, st ? st->d_carry : nullptr,
-                                    st ? st->d_ready : nullptr, flags, blocks, ctx->tile);
+                                    st ? st->d_ready : nullptr, flags, blocks, tile_of(ctx, false));
             if (nb < 0) rc = nb;
             else blocks += nb;
         }
         if (rc) break;
         prm->njobs = nj;
         prm->status = ctx->d_status;
-        rc = dispatch(ctx, *prm, blocks, false, ctx->tile);
+        rc = dispatch(ctx, *prm, blocks, false, tile_of(ctx, false));
         if (rc == SPK_OK)
             for (int k = 0; k < nj; ++k)
                 if (jobs[order[k0 + k]].state) jobs[order[k0 + k]].state->pushed += jobs[order[k0 + k]].n;
@@ -1119,7 +1240,7 @@ size_t round256(size_t n) { return (n + 255) / 256 * 256; }
 extern "C" int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t *host_stream, int H, int W,
                                             int T, float threshold, void *host_frames) {
     if (!cfg) return fail(nullptr, SPK_ERR_ARG, "cfg is NULL");
-    if (cfg->order != 1 && cfg->order != 2) return fail(nullptr, SPK_ERR_ARG, "order must be 1 or 2");
+    if (!valid_method(cfg)) return fail(nullptr, SPK_ERR_ARG, "method must be 1..4 (TFP: tfp_window 1..64)");
     if (cfg->frame_stride < 1) return fail(nullptr, SPK_ERR_ARG, "frame_stride must be >= 1");
     if (cfg->out_dtype != SPK_F32 && cfg->out_dtype != SPK_F16) return fail(nullptr, SPK_ERR_ARG, "bad out_dtype");
     if (cfg->device < 0 || cfg->device >= NOALLOC_MAX_DEVICES) return fail(nullptr, SPK_ERR_ARG, "bad device ordinal");

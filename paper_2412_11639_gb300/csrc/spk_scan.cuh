@@ -1,4 +1,5 @@
-// Per-pixel online stability scan (FSR / SSR, Sec. III-B) -- device code.
+// Per-pixel online stability scan (FSR / SSR, Sec. III-B; the TFI baseline of Sec. II as
+// ORDER 3, where every interval is its own span) -- device code.
 //
 // One instance follows one pixel through time, one spike at a time.  Every cut of S_1 it
 // finds is handed to a sink as a candidate sink.cand(t_cut, i_cut): the spike time at
@@ -85,7 +86,9 @@ struct PixelScan {
     SPK_DEV void spike(int t, Sink &sink) {
         const int x = t - last_t;
         const int i = nint;
-        if (ORDER == 1) {
+        if (ORDER == 3) {  // TFI (Sec. II): every interval is its own span
+            if (i > 0) sink.cand(last_t, i - 1);
+        } else if (ORDER == 1) {
             const int lo = min(v0, x), hi = max(v1, x);
             const bool brk = hi - lo > 1;
             if (brk) sink.cand(last_t, i - 1);  // the sequence ends at spike last_t
@@ -129,7 +132,7 @@ struct PixelScan {
     // (or has no distance yet) -- they are absorbed in O(1) and true is returned: 32
     // intervals of 1, each an S_2 distance of 1.  Otherwise nothing changes.
     SPK_DEV bool absorb_ones(int base) {
-        if (last_t != base - 1) return false;
+        if (ORDER == 3 || last_t != base - 1) return false;
         if (ORDER == 1) {
             if (v0 != 1) return false;  // [lo, hi] = [1, 1 or 2] already holds 1
         } else {

@@ -338,3 +338,41 @@ def test_theta_scales_values():
     r1 = oracle.reconstruct(st, 1, 32, 200, 1.0, 2, 3)
     r255 = oracle.reconstruct(st, 1, 32, 200, 255.0, 2, 3)
     assert np.allclose(r255.frames, 255.0 * r1.frames, rtol=1e-15)
+
+
+# ----------------------------------------------------------------- TFI / TFP (Sec. II) ----
+def test_tfi_tfp_against_literal_reading():
+    for seed in range(40):
+        b = spkgen.random_bits(80, 8, 0.05 + 0.02 * seed, 300 + seed)
+        st = spkgen.pack(b)
+        for stride in (1, 3):
+            f = oracle.tfi(st, 1, 8, 80, 1.0, stride)
+            for p in range(8):
+                assert np.allclose(f[:, p], [float(v) for v in bf.tfi_frames(b[:, p].tolist(), stride)],
+                                   rtol=1e-15, atol=0)
+            for L in (1, 7, 32):
+                g = oracle.tfp(st, 1, 8, 80, L, 1.0, stride)
+                for p in range(8):
+                    assert np.allclose(g[:, p], [float(v) for v in bf.tfp_frames(b[:, p].tolist(), L, stride)],
+                                       rtol=1e-15, atol=0)
+
+
+def test_tfi_is_fsr_of_single_intervals_and_tfp_tracks_rate():
+    """TFI equals the FSR frames of a stream whose every interval breaks the rule; TFP of a
+    constant intensity Q over a full window counts floor or ceil of L Q spikes (Eq. 2)."""
+    s = [0]
+    for i in range(30):
+        s.append(s[-1] + (2 if i % 2 == 0 else 8))
+    T = s[-1] + 5
+    bits = np.zeros((T, 1), dtype=np.uint8)
+    bits[s, 0] = 1
+    st = spkgen.pack(bits)
+    assert np.array_equal(oracle.tfi(st, 1, 1, T, 1.0, 1), oracle.reconstruct(st, 1, 1, T, 1.0, 1, 1).frames)
+    rng = np.random.default_rng(21)
+    Q = rng.uniform(0.05, 1.0, 64)
+    q = np.broadcast_to(Q, (600, 64)).copy()
+    st = spkgen.simulate_table(q, rng.uniform(0, 1, 64) * Q)
+    for L in (32, 64):
+        g = oracle.tfp(st, 1, 64, 600, L, 1.0, 1)[L:]
+        cnt = np.rint(g * L)
+        assert np.all((cnt >= np.floor(L * Q)) & (cnt <= np.ceil(L * Q)))
