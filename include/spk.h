@@ -186,6 +186,63 @@ const char *spk_last_error(const spk_ctx *ctx);
 /* Number of kernel launches this context has issued since it was created. */
 int64_t spk_launch_count(const spk_ctx *ctx);
 
+/* ------------------------------------------------------------- learned refiner ----
+ * A learned extension of the plain method (no counterpart in the paper, which is
+ * parameter free): a 5-layer 3x3 convolutional network (16 -> 32 -> 32 -> 32 -> 32 -> 1
+ * channels, ReLU, bf16 weights and activations, fp32 accumulation on the tensor cores)
+ * that reads, per pixel and frame, the plain reconstruction and the rates theta / x of the
+ * last four intervals, and returns plain + a learned correction.  Trained with the mean
+ * squared error to a ground-truth intensity (Adam).  The plain frames remain the
+ * fallback and the reference its error is judged against. */
+
+/* Refiner input for every frame of a stream: device bf16 [T_out][H][W][16] (NHWC).
+ * Channel 0 = plain[k][p] (device fp32 [T_out][H][W], e.g. the frames of spk_reconstruct
+ * with SPK_F32); channels 4..7 = threshold / x for the last four intervals x completed at
+ * or before t_k = k * stride (the most recent first, 0 where the pixel has fewer); the
+ * other channels 0.  Uses ctx's frame_stride.  Asynchronous.
+ * Errors: SPK_ERR_ARG (NULL, misaligned, not device memory), SPK_ERR_CUDA. */
+int spk_features(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold,
+                 const float *plain, void *x0);
+
+typedef struct spk_refiner spk_refiner;
+
+/* Number of fp32 parameters of the network (weights [9][Cout][Cin] and biases per layer). */
+int64_t spk_refiner_num_params(void);
+
+/* Creates a refiner on `device` with seeded He-uniform weights (the last layer scaled by
+ * 0.1 so that an untrained refiner returns about the plain value).  Allocates its
+ * parameters, Adam moments and (lazily) its activation workspace.
+ * Errors: SPK_ERR_CUDA, SPK_ERR_OOM. */
+int spk_refiner_create(int device, uint64_t seed, spk_refiner **out);
+
+/* Waits for the device and frees the refiner.  NULL is a no-op. */
+int spk_refiner_destroy(spk_refiner *r);
+
+/* Description of the last refiner failure (NULL: of the last failed create). */
+const char *spk_refiner_last_error(const spk_refiner *r);
+
+/* Loads n == spk_refiner_num_params() fp32 parameters from host memory (a checkpoint)
+ * and resets the Adam state.  Synchronous.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA. */
+int spk_refiner_set_params(spk_refiner *r, const float *host, int64_t n);
+
+/* Copies the parameters (which = 0) or the gradient of the last train step (which = 1)
+ * to host memory.  Synchronous.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA. */
+int spk_refiner_get_params(spk_refiner *r, float *host, int64_t n, int which);
+
+/* out[n][y][x] = plain + network(x0) for N frames of H x W pixels.  x0: device bf16
+ * [N][H][W][16] (spk_features), plain and out: device fp32 [N][H][W].  Runs on `stream`
+ * (a cudaStream_t, NULL = legacy default); asynchronous.  N, H < 65536.
+ * Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM. */
+int spk_refiner_forward(spk_refiner *r, void *stream, const void *x0, const float *plain, int N,
+                        int H, int W, float *out);
+
+/* One Adam step (lr, beta1 0.9, beta2 0.999) on the mean squared error between the
+ * refined frames and gt (device fp32 [N][H][W]).  If loss_host is not NULL it receives
+ * the batch's mean squared error before the step (this synchronises `stream`).
+ * Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM. */
+int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const float *plain,
+                           const float *gt, int N, int H, int W, float lr, float *loss_host);
+
 /* Diagnostic of the bounded device waits (no counterpart in the paper).  Every wait of
  * the kernels (the mbarrier waits of the stream pipeline) gives up after a bounded time
  * (about 2 s) instead of hanging, sets the timeout bit of the context's status word and

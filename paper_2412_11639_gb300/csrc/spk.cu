@@ -18,6 +18,7 @@
 // Values are known only when a sequence closes, which may be thousands of steps later
 // (a static pixel is one sequence), so rows are written when resolved, not when sampled.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -640,6 +641,112 @@ __global__ void __launch_bounds__(NTHREADS, 3) spk_tfp_kernel(const __grid_const
     }
 }
 
+// --------------------------------------------------------- refiner input features ----
+// Input of the learned refiner, NHWC bf16 with 16 channels per pixel and frame: channel 0
+// the plain reconstruction of the frame (given, fp32), channels 4..7 theta / x for the last
+// four intervals x completed at or before t_k (the most recent first; 0 where the pixel
+// has fewer), every other channel 0.  Same TMA pipeline and transpose as the scan.
+constexpr int FEAT_C = 16;
+
+template <int TT>
+__global__ void __launch_bounds__(NTHREADS, 3)
+    spk_feature_kernel(const __grid_constant__ Batch<1> prm, const float *plain, __nv_bfloat16 *x0) {
+    constexpr int WPT = TT / 32;
+    extern __shared__ uint8_t smem_raw[];
+    StageSmem<TT> &sm = *reinterpret_cast<StageSmem<TT> *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Job &job = prm.jobs[0];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NCW * 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int blk = static_cast<int>(blockIdx.x);
+    if (warp == NCW) {
+        if (lane == 0) {
+            const CUtensorMap *map = &prm.maps[0];
+            int issued = 0;
+            for (int j = 0; j < job.ntiles; ++j) {
+                const int s = j % NS;
+                if (j >= NS && !mbar_wait(&sm.empty[s], ((j / NS) - 1) & 1, prm.status)) break;
+                mbar_arrive_expect_tx(&sm.full[s], TT * ROW_BYTES);
+                tma_load_2d(&sm.stage[s][0][0], map, &sm.full[s], blk * ROW_BYTES, j * TT);
+                issued = j + 1;
+            }
+            for (int j = issued > NS ? issued - NS : 0; j < issued; ++j)
+                if (!mbar_wait(&sm.full[j % NS], (j / NS) & 1, prm.status)) break;
+        }
+        return;
+    }
+    const int64_t p = static_cast<int64_t>(blk) * BLOCK_PIX + warp * 32 + lane;
+    const bool valid = p < job.P;
+    int last_t = -1, x1 = 0, x2 = 0, x3 = 0, x4 = 0;
+    int k = 0;
+    for (int j = 0; j < job.ntiles; ++j) {
+        const int s = j % NS;
+        if (!__all_sync(FULL, mbar_wait(&sm.full[s], (j / NS) & 1, prm.status))) return;
+        uint32_t r[WPT];
+#pragma unroll
+        for (int h = 0; h < WPT; ++h) r[h] = lds_u32(&sm.stage[s][lane + 32 * h][warp * 4]);
+        fence_proxy_async_smem();
+        mbar_arrive(&sm.empty[s]);
+#pragma unroll
+        for (int h = 0; h < WPT; ++h) {
+            uint32_t w = warp_transpose32(r[h], lane);
+            if (!valid) w = 0;
+            const int base = job.t_base + j * TT + h * 32;
+            for (; k < job.T_out && k * job.stride < base + 32; ++k) {  // frames sampled here
+                const int o = k * job.stride - base;
+                const uint32_t upto = (2u << o) - 1u;
+                uint32_t now = w & upto;  // spikes at or before t_k
+                w &= ~upto;
+                while (now) {
+                    const int t = base + __ffs(now) - 1;
+                    now &= now - 1;
+                    if (last_t >= 0) {
+                        x4 = x3;
+                        x3 = x2;
+                        x2 = x1;
+                        x1 = t - last_t;
+                    }
+                    last_t = t;
+                }
+                if (valid) {
+                    const float th = job.theta;
+                    const int64_t q = static_cast<int64_t>(k) * job.P + p;
+                    __nv_bfloat162 c01 = __floats2bfloat162_rn(plain[q], 0.f);
+                    __nv_bfloat162 c45 = __floats2bfloat162_rn(x1 ? __fdiv_rn(th, static_cast<float>(x1)) : 0.f,
+                                                               x2 ? __fdiv_rn(th, static_cast<float>(x2)) : 0.f);
+                    __nv_bfloat162 c67 = __floats2bfloat162_rn(x3 ? __fdiv_rn(th, static_cast<float>(x3)) : 0.f,
+                                                               x4 ? __fdiv_rn(th, static_cast<float>(x4)) : 0.f);
+                    uint4 lo;
+                    lo.x = *reinterpret_cast<uint32_t *>(&c01);
+                    lo.y = 0u;
+                    lo.z = *reinterpret_cast<uint32_t *>(&c45);
+                    lo.w = *reinterpret_cast<uint32_t *>(&c67);
+                    uint4 *dst = reinterpret_cast<uint4 *>(x0 + q * FEAT_C);
+                    dst[0] = lo;
+                    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+            while (w) {  // the rest of the word
+                const int t = base + __ffs(w) - 1;
+                w &= w - 1;
+                if (last_t >= 0) {
+                    x4 = x3;
+                    x3 = x2;
+                    x2 = x1;
+                    x1 = t - last_t;
+                }
+                last_t = t;
+            }
+        }
+    }
+}
+
 // Self-test of the bounded waits: one warp waits on an mbarrier that nothing arrives at,
 // through the same mbar_wait the scan uses, gives up after `limit` cycles and flags the
 // status word.
@@ -1160,6 +1267,31 @@ int spk_autotune(spk_ctx *ctx, const spk_job *jobs, int njobs, int *best_tile) {
     if (best_tile) *best_tile = best;
     if (rc == SPK_OK) rc = spk_synchronize(ctx);
     return rc;
+}
+
+int spk_features(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold, const float *plain,
+                 void *x0) {
+    int rc = check_stream_args(ctx, stream, H, W, T, threshold);
+    if (rc) return rc;
+    ctx->msg[0] = 0;
+    if (!plain || !x0 || reinterpret_cast<uintptr_t>(x0) % 16 || reinterpret_cast<uintptr_t>(plain) % 4)
+        return fail(ctx, SPK_ERR_ARG, "plain or x0 is NULL or misaligned");
+    if (!is_device_ptr(stream) || !is_device_ptr(plain) || !is_device_ptr(x0))
+        return fail(ctx, SPK_ERR_ARG, "pointers must be device memory");
+    if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
+    Batch<1> prm{};
+    const int nb = fill_job(ctx, &prm.maps[0], &prm.jobs[0], stream, H, W, T, 0, T, threshold, nullptr, nullptr,
+                            nullptr, JOB_FIRST | JOB_LAST, 0, TT_DEFAULT);
+    if (nb < 0) return nb;
+    prm.njobs = 1;
+    prm.status = ctx->d_status;
+    constexpr size_t bytes = sizeof(StageSmem<TT_DEFAULT>) + 128;
+    spk_feature_kernel<TT_DEFAULT><<<nb, NTHREADS, bytes, ctx->stream>>>(prm, plain,
+                                                                          static_cast<__nv_bfloat16 *>(x0));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    ++ctx->launches;
+    return SPK_OK;
 }
 
 int spk_selftest_wait(spk_ctx *ctx, int64_t limit_cycles) {

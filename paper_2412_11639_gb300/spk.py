@@ -20,7 +20,10 @@ EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reco
            "spk_reconstruct_host", "spk_segments", "spk_synchronize", "spk_last_error",
            "spk_launch_count", "spk_reconstruct_host_noalloc", "spk_selftest_wait", "spk_stream_open",
            "spk_stream_close", "spk_stream_steps", "spk_stream_ready", "spk_run", "spk_set_tile",
-           "spk_get_tile", "spk_autotune")
+           "spk_get_tile", "spk_autotune", "spk_features", "spk_refiner_num_params",
+           "spk_refiner_create", "spk_refiner_destroy", "spk_refiner_last_error",
+           "spk_refiner_set_params", "spk_refiner_get_params", "spk_refiner_forward",
+           "spk_refiner_train_step")
 SPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -89,6 +92,24 @@ def load(path: str | None = None):
     lib.spk_get_tile.restype = i32
     lib.spk_autotune.argtypes = [vp, _c.POINTER(spk_job), i32, _c.POINTER(i32)]
     lib.spk_autotune.restype = i32
+    lib.spk_features.argtypes = [vp, vp, i32, i32, i32, f32, vp, vp]
+    lib.spk_features.restype = i32
+    lib.spk_refiner_num_params.argtypes = []
+    lib.spk_refiner_num_params.restype = i64
+    lib.spk_refiner_create.argtypes = [i32, _c.c_uint64, _c.POINTER(vp)]
+    lib.spk_refiner_create.restype = i32
+    lib.spk_refiner_destroy.argtypes = [vp]
+    lib.spk_refiner_destroy.restype = i32
+    lib.spk_refiner_last_error.argtypes = [vp]
+    lib.spk_refiner_last_error.restype = _c.c_char_p
+    lib.spk_refiner_set_params.argtypes = [vp, vp, i64]
+    lib.spk_refiner_set_params.restype = i32
+    lib.spk_refiner_get_params.argtypes = [vp, vp, i64, i32]
+    lib.spk_refiner_get_params.restype = i32
+    lib.spk_refiner_forward.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp]
+    lib.spk_refiner_forward.restype = i32
+    lib.spk_refiner_train_step.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, f32, _c.POINTER(f32)]
+    lib.spk_refiner_train_step.restype = i32
     lib.spk_selftest_wait.argtypes = [vp, i64]
     lib.spk_selftest_wait.restype = i32
     lib.spk_reconstruct_host_noalloc.argtypes = [_c.POINTER(spk_config), vp, i32, i32, i32, f32, vp]
@@ -226,3 +247,47 @@ def spk_autotune(ctx, jobs) -> int:
     best = _c.c_int()
     _check(ctx, load().spk_autotune(ctx, _jobs(jobs), len(jobs), _c.byref(best)))
     return best.value
+
+
+def spk_features(ctx, stream, H, W, T, threshold, plain, x0):
+    return _check(ctx, load().spk_features(ctx, _addr(stream), H, W, T, threshold, _addr(plain), _addr(x0)))
+
+
+def _rcheck(r, rc):
+    if rc != SPK_OK:
+        msg = load().spk_refiner_last_error(r)
+        raise SpkError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def spk_refiner_num_params() -> int:
+    return load().spk_refiner_num_params()
+
+
+def spk_refiner_create(device: int = 0, seed: int = 0):
+    out = _c.c_void_p()
+    _rcheck(None, load().spk_refiner_create(device, seed, _c.byref(out)))
+    return out
+
+
+def spk_refiner_destroy(r):
+    return load().spk_refiner_destroy(r)
+
+
+def spk_refiner_set_params(r, host):
+    return _rcheck(r, load().spk_refiner_set_params(r, _addr(host), len(host)))
+
+
+def spk_refiner_get_params(r, host, which: int = 0):
+    return _rcheck(r, load().spk_refiner_get_params(r, _addr(host), len(host), which))
+
+
+def spk_refiner_forward(r, stream, x0, plain, N, H, W, out):
+    return _rcheck(r, load().spk_refiner_forward(r, stream, _addr(x0), _addr(plain), N, H, W, _addr(out)))
+
+
+def spk_refiner_train_step(r, stream, x0, plain, gt, N, H, W, lr, want_loss=True):
+    loss = _c.c_float(float("nan"))
+    _rcheck(r, load().spk_refiner_train_step(r, stream, _addr(x0), _addr(plain), _addr(gt), N, H, W, lr,
+                                             _c.byref(loss) if want_loss else None))
+    return loss.value

@@ -95,3 +95,19 @@ def test_noalloc_rejects_oversize_before_device_work(lib):
     with pytest.raises(spk.SpkError) as e:
         spk.spk_reconstruct_host_noalloc(st, 1, 8, 4, float("nan"), out)
     assert e.value.code == spk.SPK_ERR_ARG
+
+
+def test_refiner_host_checks(lib):
+    import torch
+    # 9 * Cin * Cout + Cout per layer for 16 -> 32 -> 32 -> 32 -> 32 -> 16
+    assert spk.spk_refiner_num_params() == 9 * 16 * 32 + 32 + 3 * (9 * 32 * 32 + 32) + 9 * 32 * 16 + 16
+    assert lib.spk_refiner_destroy(None) == spk.SPK_OK
+    assert lib.spk_refiner_create(0, 0, None) == spk.SPK_ERR_ARG
+    assert lib.spk_refiner_forward(None, None, None, None, 1, 1, 1, None) == spk.SPK_ERR_ARG
+    assert lib.spk_refiner_train_step(None, None, None, None, None, 1, 1, 1, 0.0, None) == spk.SPK_ERR_ARG
+    assert lib.spk_refiner_set_params(None, None, 0) == spk.SPK_ERR_ARG
+    assert lib.spk_features(None, None, 1, 1, 1, 1.0, None, None) == spk.SPK_ERR_ARG
+    if not torch.cuda.is_available():
+        with pytest.raises(spk.SpkError) as e:
+            spk.spk_refiner_create(0, 1)
+        assert e.value.code == spk.SPK_ERR_CUDA

@@ -1,0 +1,198 @@
+"""Learned refiner on the GPU: features, forward, gradients and Adam against plain PyTorch
+fp32 on the CPU (tests/refnet.py), and training on simulator streams against the plain
+reconstruction (PSNR, SSIM)."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2412_11639_gb300 as pkg
+import spkgen
+from paper_2412_11639_gb300 import quality, refiner, spk
+
+torch = pytest.importorskip("torch")
+import refnet  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    pkg.build()
+    spk.load()
+
+
+def _bf16_bits(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).view(torch.int16).numpy()
+
+
+def _cpu_features(stream, H, W, T, stride, plain, theta):
+    """Channel 0 plain, 4..7 theta / x of the last four intervals ending at or before t_k."""
+    P = H * W
+    bits = np.unpackbits(stream[:T], axis=1, bitorder="little")[:, :P]
+    T_out = (T + stride - 1) // stride
+    f = np.zeros((T_out, P, 16), dtype=np.float32)
+    f[:, :, 0] = plain.reshape(T_out, P)
+    th = np.float32(theta)
+    for p in range(P):
+        s = np.flatnonzero(bits[:, p])
+        for k in range(T_out):
+            j = int(np.searchsorted(s, k * stride, side="right"))   # spikes at or before t_k
+            for m in range(4):
+                if j - m - 2 >= 0:
+                    f[k, p, 4 + m] = th / np.float32(s[j - m - 1] - s[j - m - 2])
+    return f.reshape(T_out, H, W, 16)
+
+
+@pytest.mark.parametrize("H,W,T,stride,theta", [(23, 37, 700, 10, 1.0), (9, 130, 300, 1, 2.5)])
+def test_features_exact(H, W, T, stride, theta):
+    w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=H, W=W, T=T, stride=stride)
+    stream, _ = spkgen.make_stream(w)
+    rec = pkg.Reconstructor(order=2, stride=stride)
+    dev = torch.from_numpy(stream).cuda()
+    plain = rec(dev, H, W, T, theta)
+    x0 = refiner.features(rec, dev, H, W, T, plain, theta)
+    torch.cuda.synchronize()
+    want = _cpu_features(stream, H, W, T, stride, plain.cpu().numpy(), theta)
+    got = x0.view(torch.int16).cpu().numpy()
+    assert np.array_equal(got, _bf16_bits(want))
+
+
+def _rand_case(N, H, W, seed):
+    rng = np.random.default_rng(seed)
+    x0 = np.zeros((N, H, W, 16), dtype=np.float32)
+    x0[..., 0] = rng.uniform(0.02, 1.0, (N, H, W))
+    x0[..., 4:8] = rng.uniform(0.0, 1.0, (N, H, W, 4))
+    x0 = torch.as_tensor(x0).to(torch.bfloat16).float().numpy()   # bf16 values
+    plain = x0[..., 0].copy()
+    gt = np.clip(plain + 0.05 * rng.standard_normal((N, H, W)), 0.02, 1.0).astype(np.float32)
+    return x0, plain, gt
+
+
+def _dev(a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    return t.to(dtype) if dtype is not None else t
+
+
+@pytest.mark.parametrize("N,H,W", [(2, 20, 150), (1, 3, 5), (3, 17, 128)])
+def test_forward_matches_reference(N, H, W):
+    ref = refiner.Refiner(seed=11)
+    p = ref.params()
+    # larger last layer than the init's 0.1 scale so that the correction is not tiny
+    p[refnet.NPARAM - (9 * 32 * 16 + 16):] *= 10
+    p[-16:] = 0.01
+    ref.set_params(p)
+    x0, plain, gt = _rand_case(N, H, W, seed=N * 1000 + W)
+    out = ref(_dev(x0, torch.bfloat16), _dev(plain))
+    torch.cuda.synchronize()
+    want, _, _ = refnet.forward(p, x0, plain)
+    got = out.cpu().numpy()
+    corr = np.abs(want - plain).max()
+    assert corr > 1e-3
+    err = np.abs(got - want).max()
+    assert err <= 1e-2 * corr + 1e-6, (err, corr)
+    ref.close()
+
+
+def test_gradients_and_loss_match_reference():
+    N, H, W = 2, 21, 140
+    ref = refiner.Refiner(seed=5)
+    p = ref.params()
+    p[refnet.NPARAM - (9 * 32 * 16 + 16):] *= 10
+    ref.set_params(p)
+    x0, plain, gt = _rand_case(N, H, W, seed=7)
+    loss = ref.train_step(_dev(x0, torch.bfloat16), _dev(plain), _dev(gt), lr=0.0)
+    g = ref.grads()
+    out_ref, loss_ref, g_ref = refnet.forward(p, x0, plain, gt)
+    assert math.isclose(loss, loss_ref, rel_tol=1e-3)
+    assert np.array_equal(ref.params(), p)                     # lr 0 leaves the weights
+    for (wo, w, bo, b) in refnet.layers(p):
+        for a, n in ((wo, w.numel()), (bo, b.numel())):
+            gg, gr = g[a:a + n], g_ref[a:a + n]
+            if not np.any(gr):
+                assert np.abs(gg).max() <= 1e-9
+                continue
+            rel = np.linalg.norm(gg - gr) / np.linalg.norm(gr)
+            assert rel < 3e-2, (a, rel)
+    ref.close()
+
+
+def test_adam_first_step_moves_by_lr_times_sign():
+    # Adam's bias-corrected first step is lr * g / (|g| + eps): lr * sign(g) where |g| >> eps
+    N, H, W = 1, 16, 64
+    ref = refiner.Refiner(seed=3)
+    p0 = ref.params()
+    x0, plain, gt = _rand_case(N, H, W, seed=1)
+    args = (_dev(x0, torch.bfloat16), _dev(plain), _dev(gt))
+    ref.train_step(*args, lr=0.0)
+    g = ref.grads()
+    ref.set_params(p0)                                        # also resets the Adam state
+    ref.train_step(*args, lr=1e-3)
+    d = ref.params() - p0
+    big = np.abs(g) > 1e-5
+    assert big.sum() > 1000
+    assert np.allclose(d[big], -1e-3 * np.sign(g[big]), rtol=1e-3, atol=1e-9)
+    assert np.all(np.abs(d) <= 1e-3 * (1 + 1e-5))
+    ref.close()
+
+
+def test_params_roundtrip_and_checkpoint(tmp_path):
+    a = refiner.Refiner(seed=1)
+    b = refiner.Refiner(seed=2)
+    assert not np.array_equal(a.params(), b.params())
+    a.save(str(tmp_path / "w.npy"))
+    b.load(str(tmp_path / "w.npy"))
+    assert np.array_equal(a.params(), b.params())
+    x0, plain, _ = _rand_case(1, 8, 40, seed=2)
+    oa = a(_dev(x0, torch.bfloat16), _dev(plain))
+    ob = b(_dev(x0, torch.bfloat16), _dev(plain))
+    assert torch.equal(oa, ob)
+    with pytest.raises(spk.SpkError):
+        spk.spk_refiner_set_params(a.r, np.zeros(5, dtype=np.float32))
+    a.close()
+    b.close()
+
+
+def test_argument_errors():
+    r = refiner.Refiner(seed=0)
+    x0, plain, _ = _rand_case(1, 4, 8, seed=0)
+    host = np.zeros((1, 4, 8), dtype=np.float32)
+    with pytest.raises(spk.SpkError) as e:
+        spk.spk_refiner_forward(r.r, None, _dev(x0, torch.bfloat16), host, 1, 4, 8, _dev(plain))
+    assert e.value.code == spk.SPK_ERR_ARG
+    with pytest.raises(spk.SpkError):
+        spk.spk_refiner_forward(r.r, None, _dev(x0, torch.bfloat16), _dev(plain), 0, 4, 8, _dev(plain))
+    r.close()
+
+
+def _clip(rec, w):
+    stream, gt = spkgen.make_stream(w, gt_stride=w.stride)
+    dev = torch.from_numpy(stream).cuda()
+    plain = rec(dev, w.H, w.W, w.T)
+    x0 = refiner.features(rec, dev, w.H, w.W, w.T, plain)
+    gt_d = torch.from_numpy(gt).cuda().view(w.T_out, w.H, w.W)
+    return x0, plain, gt_d
+
+
+def test_training_beats_plain_on_held_out_stream():
+    base = spkgen.WORKLOADS["dynamic_250x400x20000"]
+    rec = pkg.Reconstructor(order=2, stride=base.stride)
+    clips = [_clip(rec, base.resized(H=64, W=128, T=4000, seed=s)) for s in (21, 22, 23, 24)]
+    test = _clip(rec, base.resized(H=64, W=128, T=4000, seed=31))
+    ref = refiner.Refiner(seed=0)
+    losses = refiner.fit(ref, clips, steps=600, lr=2e-3, batch=16)
+    out = ref(test[0], test[1])
+    torch.cuda.synchronize()
+    k0 = 20                                    # skip the head fill before the first spans close
+    gt = test[2][k0:].cpu().numpy()
+    plain = test[1][k0:].cpu().numpy()
+    refined = out[k0:].cpu().numpy()
+    p_plain, p_ref = quality.psnr(plain, gt), quality.psnr(refined, gt)
+    s_plain, s_ref = quality.ssim(plain, gt), quality.ssim(refined, gt)
+    print(f"PSNR plain {p_plain:.2f} refined {p_ref:.2f}; SSIM plain {s_plain:.4f} refined {s_ref:.4f}; "
+          f"loss {losses[0]:.3e} -> {losses[-1]:.3e}")
+    assert p_ref > p_plain + 1.0
+    assert s_ref > s_plain
+    ref.close()
