@@ -47,9 +47,13 @@ def parse_args(argv=None):
     ap.add_argument("--tfp-window", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["single", "batch", "serve"], default="single",
+    ap.add_argument("--mode", choices=["single", "batch", "serve", "refine"], default="single",
                     help="single: the headline workload; batch: 64 uneven streams per launch "
-                         "(CUDA graph, autotuned tile); serve: live streams arriving over time")
+                         "(CUDA graph, autotuned tile); serve: live streams arriving over time; "
+                         "refine: train the learned refiner on simulated clips, then evaluate it")
+    ap.add_argument("--no-refiner", action="store_true",
+                    help="single mode: skip the refiner evaluation on the headline stream")
+    ap.add_argument("--refine-clips", type=int, default=200)
     return ap.parse_args(argv)
 
 
@@ -143,11 +147,16 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------- inputs ----
-def workload_stream(name: str, rank: int, world: int):
-    """Generate (rank 0, cached in the temp dir) and load the workload's packed stream."""
+def workload_stream(name: str, rank: int, world: int, device: int | None = None):
+    """The workload's packed stream as a host array: made by the GPU generator when a device
+    is given (the same bits as the C generator), else by the C generator (rank 0, cached in
+    the temp dir)."""
     import numpy as np
     import spkgen
     w = spkgen.WORKLOADS[name]
+    if device is not None:
+        st, _ = spkgen.make_stream_cuda(w, device=device)
+        return w, st.cpu().numpy()
     cache = os.path.join(tempfile.gettempdir(), f"spk_stream_{name}.npy")
     if rank == 0 and not os.path.exists(cache):
         st, _ = spkgen.make_stream(w)
@@ -169,9 +178,8 @@ def measured_peak():
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     cdir = os.path.join(ROOT, "paper_2412_11639_gb300", "csrc")
-    for f in sorted(os.listdir(cdir)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(cdir, f), "rb").read())
+    for f in ("spk.cu", "spk_scan.cuh"):           # the scan kernel's translation unit
+        h.update(open(os.path.join(cdir, f), "rb").read())
     return h.hexdigest()
 
 
@@ -270,7 +278,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_2412_11639_gb300 import spk
 
     torch.cuda.set_device(local_rank)
-    w, st = workload_stream(args.workload, rank, world)
+    w, st = workload_stream(args.workload, rank, world, device=local_rank)
     dtype = torch.float16 if w.out_dtype == "f16" else torch.float32
     esz = 2 if dtype == torch.float16 else 4
     R = pkg.Reconstructor(order=args.order, stride=w.stride, dtype=dtype, device=local_rank,
@@ -327,6 +335,19 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(st.nbytes), "d2h_bytes_per_step": int(h_out.numel() * esz)}
     R.close()
 
+    refined = None
+    if (rank == 0 and not args.no_refiner and w.name == "dynamic_250x400x20000" and args.order == 2):
+        from paper_2412_11639_gb300 import refiner
+        if os.path.exists(refiner.CHECKPOINT):
+            rec2 = pkg.Reconstructor(order=2, stride=w.stride, device=local_rank)
+            ref = refiner.Refiner(device=local_rank)
+            ref.load(refiner.CHECKPOINT)
+            refined = refiner_eval(ref, rec2, w)
+            ref.close()
+            rec2.close()
+        else:
+            refined = {"unavailable": "no trained checkpoint in the package"}
+
     if rank != 0:
         return 0
     cpu = None
@@ -349,8 +370,127 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
+        "refiner": refined,
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------- learned refiner ----
+# multiply-adds per pixel-frame of the network as defined (inputs: the plain value and four
+# interval rates): 3x3 x (5*32 + 3*32*32 + 32*1); the kernels pad 5 -> 16 input and 1 -> 16
+# output channels to the tensor-core k16/n8 shapes and so execute 3x3 x (16*32 + 3*32*32 + 32*16)
+REFINER_MACS = 9 * (5 * 32 + 3 * 32 * 32 + 32 * 1)
+REFINER_MACS_PADDED = 9 * (16 * 32 + 3 * 32 * 32 + 32 * 16)
+
+
+def refiner_eval(ref, rec, w, chunk: int = 100, reps: int = 3, ssim_every: int = 20, skip: int = 20):
+    """Refined vs plain frames of workload w against its ground truth, and the refiner's
+    device throughput (features + forward) with CUDA events."""
+    import numpy as np
+    import torch
+
+    import spkgen
+    from paper_2412_11639_gb300 import quality, refiner
+    stream, gt = spkgen.make_stream_cuda(w, gt_stride=w.stride, device=ref.device)
+    gt = gt.view(w.T_out, w.H, w.W)
+    plain = rec(stream, w.H, w.W, w.T)
+    x0 = refiner.features(rec, stream, w.H, w.W, w.T, plain)
+    out = torch.empty_like(plain)
+    cs = rec.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def run():
+        ev[0].record(cs)
+        refiner.spk.spk_features(rec.ctx, stream, w.H, w.W, w.T, 1.0, plain, x0)
+        ev[1].record(cs)
+        for k in range(0, w.T_out, chunk):
+            n = min(chunk, w.T_out - k)
+            refiner.spk.spk_refiner_forward(ref.r, cs.cuda_stream, x0[k:k + n], plain[k:k + n], n, w.H, w.W,
+                                            out[k:k + n])
+        ev[2].record(cs)
+    run()
+    torch.cuda.synchronize()
+    feat_ms, fwd_ms = [], []
+    for _ in range(reps):
+        run()
+        torch.cuda.synchronize()
+        feat_ms.append(ev[0].elapsed_time(ev[1]))
+        fwd_ms.append(ev[1].elapsed_time(ev[2]))
+    fm, gm = statistics.median(feat_ms), statistics.median(fwd_ms)
+    pf = w.P * w.T_out
+
+    def psnr_dev(a):
+        mse = torch.mean((a[skip:].double() - gt[skip:].double()) ** 2).item()
+        return 10 * np.log10(1.0 / mse)
+    sel = slice(skip, w.T_out, ssim_every)
+    g_h = gt[sel].cpu().numpy()
+    res = {"checkpoint": os.path.relpath(refiner.CHECKPOINT, ROOT),
+           "eval_stream": w.name, "frames_scored": w.T_out - skip,
+           "psnr_plain_db": psnr_dev(plain), "psnr_refined_db": psnr_dev(out),
+           "ssim_plain": quality.ssim(plain[sel].cpu().numpy(), g_h),
+           "ssim_refined": quality.ssim(out[sel].cpu().numpy(), g_h),
+           "ssim_frames": len(range(w.T_out)[sel]),
+           "throughput_Gpf_s": pf / ((fm + gm) / 1e3) / 1e9,
+           "features_ms": fm, "forward_ms": gm, "forward_launches": 5 * ((w.T_out + chunk - 1) // chunk)}
+    res["psnr_gain_db"] = res["psnr_refined_db"] - res["psnr_plain_db"]
+    peak = bf16_peak()
+    tf = pf * 2 * REFINER_MACS / (gm / 1e3) / 1e12
+    tfp = pf * 2 * REFINER_MACS_PADDED / (gm / 1e3) / 1e12
+    res["roofline"] = {"bound": "tensor", "achieved": tf, "peak": peak[0], "unit": "TFLOP/s", "frac": tf / peak[0],
+                       "peak_source": peak[1], "executed_TFLOP_s": tfp,
+                       "flop_per_pixel_frame": 2 * REFINER_MACS,
+                       "executed_flop_per_pixel_frame": 2 * REFINER_MACS_PADDED}
+    del x0, stream
+    return res
+
+
+def bf16_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["bf16_tflops"]), "measured bf16_tflops (burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def run_refine(args):
+    """Train the refiner on freshly simulated clips, then evaluate it on the headline stream."""
+    import torch
+
+    import paper_2412_11639_gb300 as pkg
+    import spkgen
+    from paper_2412_11639_gb300 import refiner
+    base = spkgen.WORKLOADS["dynamic_250x400x20000"]
+    rec = pkg.Reconstructor(order=2, stride=base.stride)
+    ref = refiner.Refiner(seed=0)
+    clip = base.resized(T=2000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = refiner.train_on_simulator(ref, rec, clip, args.refine_clips, steps_per_clip=2, batch=16)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    # the training step alone (features and clips excluded), timed with CUDA events
+    x0, plain, gt = refiner.simulator_clip(rec, clip.resized(seed=999))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        ref.train_step(x0[:16], plain[:16], gt[:16], 1e-5, want_loss=False)
+    e0.record(ref.stream)
+    for _ in range(10):
+        ref.train_step(x0[:16], plain[:16], gt[:16], 1e-5, want_loss=False)
+    e1.record(ref.stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / 10
+    res = refiner_eval(ref, rec, base)
+    line = {"mode": "refine", "metric": "refiner PSNR gain vs plain (dB) and throughput",
+            "training": {"clips": args.refine_clips, "clip": f"{clip.H}x{clip.W}x{clip.T} stride {clip.stride}",
+                         "steps": 2 * args.refine_clips, "batch_frames": 16, "seconds": dt,
+                         "first_loss": losses[0], "last_loss": losses[-1],
+                         "train_step_ms": step_ms,
+                         "train_Gpf_s": 16 * clip.P / (step_ms / 1e3) / 1e9},
+            "refiner": res, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    ref.close()
+    rec.close()
     return 0
 
 
@@ -459,7 +599,7 @@ def main(argv=None):
     if args.mode != "single" and args.impl == "ours":
         if world > 1 and rank != 0:
             return 0
-        return run_batch(args) if args.mode == "batch" else run_serve(args)
+        return {"batch": run_batch, "serve": run_serve, "refine": run_refine}[args.mode](args)
     if world > 1:
         import torch
         import torch.distributed as dist

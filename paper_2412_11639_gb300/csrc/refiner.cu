@@ -359,8 +359,11 @@ LayerPtrs layer_ptrs(spk_refiner *r) {
     return lp;
 }
 
-int ensure_buffers(spk_refiner *r, int64_t pixels) {
-    if (pixels <= r->cap) return SPK_OK;
+// activation workspace for `pixels` pixel-frames: four activation buffers when training,
+// two for inference; grown on demand, never shrunk
+int ensure_buffers(spk_refiner *r, int64_t pixels, bool train) {
+    if (pixels <= r->cap && (!train || r->grad[0])) return SPK_OK;
+    pixels = pixels > r->cap ? pixels : r->cap;
     for (int l = 0; l < NL; ++l)
         if (r->act[l]) cudaFree(r->act[l]), r->act[l] = nullptr;
     for (int k = 0; k < 2; ++k)
@@ -368,9 +371,11 @@ int ensure_buffers(spk_refiner *r, int64_t pixels) {
     if (r->out) cudaFree(r->out), r->out = nullptr;
     r->cap = 0;
     bool ok = true;
-    for (int l = 0; l < NL - 1; ++l) ok &= cudaMalloc(&r->act[l], pixels * 32 * sizeof(bf16)) == cudaSuccess;
-    for (int k = 0; k < 2; ++k) ok &= cudaMalloc(&r->grad[k], pixels * 32 * sizeof(bf16)) == cudaSuccess;
-    ok &= cudaMalloc(&r->out, pixels * sizeof(float)) == cudaSuccess;
+    for (int l = 0; l < (train ? NL - 1 : 2); ++l) ok &= cudaMalloc(&r->act[l], pixels * 32 * sizeof(bf16)) == cudaSuccess;
+    if (train) {
+        for (int k = 0; k < 2; ++k) ok &= cudaMalloc(&r->grad[k], pixels * 32 * sizeof(bf16)) == cudaSuccess;
+        ok &= cudaMalloc(&r->out, pixels * sizeof(float)) == cudaSuccess;
+    }
     if (!ok) {
         cudaGetLastError();
         return rfail(r, SPK_ERR_OOM, "refiner workspace allocation failed");
@@ -379,15 +384,18 @@ int ensure_buffers(spk_refiner *r, int64_t pixels) {
     return SPK_OK;
 }
 
-// forward through all layers; activations of L0..L3 kept in r->act
-int forward(spk_refiner *r, cudaStream_t s, const bf16 *x0, const float *plain, int N, int H, int W, float *out) {
+// forward through all layers; for training the activations of L0..L3 stay in r->act[0..3]
+// (the backward pass reads them), for inference two of them are used in turn
+int forward(spk_refiner *r, cudaStream_t s, const bf16 *x0, const float *plain, int N, int H, int W, float *out,
+            bool keep) {
     dim3 grid((W + MT - 1) / MT, H, N);
-    conv<16, 32, 0>(s, grid, x0, r->wt[0], r->w + layer_off(0) + layer_w(0), r->act[0], nullptr, nullptr, H, W);
+    auto act = [&](int l) { return r->act[keep ? l : (l & 1)]; };
+    conv<16, 32, 0>(s, grid, x0, r->wt[0], r->w + layer_off(0) + layer_w(0), act(0), nullptr, nullptr, H, W);
     for (int l = 1; l < NL - 1; ++l)
-        conv<32, 32, 0>(s, grid, r->act[l - 1], r->wt[l], r->w + layer_off(l) + layer_w(l), r->act[l], nullptr,
-                        nullptr, H, W);
-    conv<32, 16, 2>(s, grid, r->act[NL - 2], r->wt[NL - 1], r->w + layer_off(NL - 1) + layer_w(NL - 1), out,
-                    nullptr, plain, H, W);
+        conv<32, 32, 0>(s, grid, act(l - 1), r->wt[l], r->w + layer_off(l) + layer_w(l), act(l), nullptr, nullptr,
+                        H, W);
+    conv<32, 16, 2>(s, grid, act(NL - 2), r->wt[NL - 1], r->w + layer_off(NL - 1) + layer_w(NL - 1), out, nullptr,
+                    plain, H, W);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPK_OK : rfail(r, SPK_ERR_CUDA, "refiner forward: %s", cudaGetErrorString(e));
 }
@@ -502,9 +510,9 @@ int spk_refiner_forward(spk_refiner *r, void *stream, const void *x0, const floa
         return rfail(r, SPK_ERR_ARG, "x0, plain, out must be device memory (x0 16-byte aligned)");
     if (N > 65535 || H > 65535) return rfail(r, SPK_ERR_ARG, "N and H must be < 65536");
     cudaSetDevice(r->device);
-    int rc = ensure_buffers(r, static_cast<int64_t>(N) * H * W);
+    int rc = ensure_buffers(r, static_cast<int64_t>(N) * H * W, false);
     if (rc) return rc;
-    return forward(r, static_cast<cudaStream_t>(stream), static_cast<const bf16 *>(x0), plain, N, H, W, out);
+    return forward(r, static_cast<cudaStream_t>(stream), static_cast<const bf16 *>(x0), plain, N, H, W, out, false);
 }
 
 int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const float *plain, const float *gt, int N,
@@ -518,11 +526,11 @@ int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const f
     if (N > 65535 || H > 65535) return rfail(r, SPK_ERR_ARG, "N and H must be < 65536");
     cudaSetDevice(r->device);
     const int64_t P = static_cast<int64_t>(N) * H * W;
-    int rc = ensure_buffers(r, P);
+    int rc = ensure_buffers(r, P, true);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bf16 *x = static_cast<const bf16 *>(x0);
-    rc = forward(r, s, x, plain, N, H, W, r->out);
+    rc = forward(r, s, x, plain, N, H, W, r->out, true);
     if (rc) return rc;
     cudaMemsetAsync(r->g, 0, NPARAM * sizeof(float), s);
     cudaMemsetAsync(r->loss, 0, sizeof(float), s);

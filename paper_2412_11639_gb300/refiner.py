@@ -97,3 +97,44 @@ def fit(ref: Refiner, clips, steps: int, lr: float = 1e-3, batch: int = 8, seed:
         losses.append(ref.train_step(x0[k:k + n], plain[k:k + n], gt[k:k + n], a,
                                      want_loss=(s % 10 == 0 or s == steps - 1)))
     return losses
+
+
+CHECKPOINT = __import__("os").path.join(__import__("os").path.dirname(__file__), "weights",
+                                        "refiner_dynamic.npy")
+
+
+def simulator_clip(rec, w, device: int = 0):
+    """(x0, plain, gt) of one simulated clip: the stream and its ground truth come from the
+    GPU generator, the plain frames from rec, the features from spk_features."""
+    import spkgen
+    torch = rec.torch
+    stream, gt = spkgen.make_stream_cuda(w, gt_stride=w.stride, device=device)
+    plain = rec(stream, w.H, w.W, w.T)
+    x0 = features(rec, stream, w.H, w.W, w.T, plain)
+    del stream
+    return x0, plain, gt.view(w.T_out, w.H, w.W)
+
+
+def train_on_simulator(ref: Refiner, rec, base, n_clips: int, steps_per_clip: int = 4, batch: int = 16,
+                       lr: float = 2e-3, lr_final: float = 2e-4, seed0: int = 1000, log=None):
+    """Train on n_clips freshly simulated clips of recipe `base` (seeds seed0, seed0+1, ...),
+    steps_per_clip Adam steps of `batch` consecutive frames each, learning rate decaying
+    linearly from lr to lr_final.  Returns the mean loss of every clip's steps."""
+    rng = np.random.Generator(np.random.PCG64(seed0))
+    total = n_clips * steps_per_clip
+    out = []
+    s = 0
+    for c in range(n_clips):
+        x0, plain, gt = simulator_clip(rec, base.resized(seed=seed0 + c), ref.device)
+        ls = []
+        for _ in range(steps_per_clip):
+            k = int(rng.integers(0, plain.shape[0] - batch + 1))
+            a = lr + (lr_final - lr) * s / max(1, total - 1)
+            ls.append(ref.train_step(x0[k:k + batch], plain[k:k + batch], gt[k:k + batch], a,
+                                     want_loss=(c % 50 == 0)))
+            s += 1
+        if c % 50 == 0:
+            out.append(float(np.mean(ls)))
+            if log:
+                log(f"clip {c}/{n_clips} loss {out[-1]:.4e}")
+    return out

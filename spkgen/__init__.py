@@ -29,13 +29,25 @@ _SO = os.path.join(_HERE, "_spkgen.so")
 _lib = None
 
 
+_CU_SRC = os.path.join(_HERE, "gen.cu")
+_CU_SO = os.path.join(_HERE, "_spkgen_cuda.so")
+_culib = None
+
+
 def build(force: bool = False) -> str:
-    """Compile gen.c into an in-tree shared library (plain C, OpenMP, no FMA contraction)."""
+    """Compile gen.c (plain C, OpenMP, no FMA contraction) and gen.cu (the GPU twin, sm_103a,
+    -fmad=false) into in-tree shared libraries."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
                                "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
+    if force or not os.path.exists(_CU_SO) or os.path.getmtime(_CU_SO) < os.path.getmtime(_CU_SRC):
+        tmp = _CU_SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                               "-fmad=false", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+                               _CU_SRC, "-o", tmp])
+        os.replace(tmp, _CU_SO)
     return _SO
 
 
@@ -228,3 +240,47 @@ def random_bits(T: int, P: int, density: float, seed: int) -> np.ndarray:
 def uniform(seed: int, stream: int, a: int, b: int) -> float:
     """The counter-based uniform the simulator draws (exposed for the pins)."""
     return _load().spkgen_uniform(seed, stream, a, b)
+
+
+def _load_cuda():
+    global _culib
+    if _culib is None:
+        build()
+        lib = ctypes.CDLL(_CU_SO)
+        c = ctypes
+        lib.spkgen_cuda_simulate.argtypes = [c.c_void_p, c.c_int64, c.c_int, c.c_int, c.c_int,
+                                             c.c_void_p, c.c_int, c.c_double, c.c_double,
+                                             c.c_double, c.c_double, c.c_int, c.c_void_p,
+                                             c.c_double, c.c_double, c.c_double, c.c_uint64,
+                                             c.c_double, c.c_void_p, c.c_int, c.c_void_p]
+        lib.spkgen_cuda_simulate.restype = c.c_int
+        _culib = lib
+    return _culib
+
+
+def make_stream_cuda(w: Workload, gt_stride: int | None = None, device: int = 0, stream=None):
+    """make_stream on the GPU (gen.cu): the same bits, as torch CUDA tensors.
+
+    Returns (stream uint8 [T][pitch], gt float32 [ceil(T/gt_stride)][H*W] or None).  The
+    texture table is rendered on the host exactly as for make_stream.
+    """
+    import torch
+    sc = scene(w)
+    dev = f"cuda:{device}"
+    tex = torch.from_numpy(sc.tex).to(dev)
+    out = torch.empty((w.T, w.pitch), dtype=torch.uint8, device=dev)
+    gt = None
+    if gt_stride:
+        gt = torch.empty((num_frames(w.T, gt_stride), w.P), dtype=torch.float32, device=dev)
+    ev = np.ascontiguousarray(sc.events)
+    cs = stream if stream is not None else torch.cuda.current_stream(device)
+    rc = _load_cuda().spkgen_cuda_simulate(out.data_ptr(), w.pitch, w.H, w.W, w.T, tex.data_ptr(),
+                                           w.L, sc.x0, sc.y0, sc.vx, sc.vy, ev.shape[0],
+                                           ev.ctypes.data if ev.size else None, w.ilo, w.ihi,
+                                           w.theta, w.seed, w.noise_p,
+                                           gt.data_ptr() if gt is not None else None,
+                                           gt_stride or 0, cs.cuda_stream)
+    if rc != 0:
+        raise ValueError(f"spkgen_cuda_simulate failed ({rc})")
+    cs.synchronize()           # tex is freed when this function returns
+    return out, gt
