@@ -182,19 +182,22 @@ __device__ __forceinline__ float seq_value(float theta, int n, int d) {
 }
 
 // --------------------------------------------------------------------- sinks ----
-// Cuts of one lane, in time order, in a per-lane shared-memory ring of (t_cut, i_cut).
-// Stable spans run between consecutive cuts, so span j has N = i_j - i_{j-1} intervals
-// over D = t_j - t_{j-1} steps; the first starts at the first spike with index -1.  A
-// candidate that arrives one place early (a retroactive S_2 cut) is swapped in front of
-// the last cut.  Only cuts at or before the scan's frontier are final; the row flush
-// consumes nothing beyond the last final cut.  The pixel's last record is TAIL: it
-// holds the last value for the frames after the last spike (0 if there is no span).
+// Cuts of one lane, in time order, in a per-lane shared-memory ring.  Stable spans run
+// between consecutive cuts, so span j has N = i_j - i_{j-1} intervals over
+// D = t_j - t_{j-1} steps; the first starts at the first spike with index -1.  A candidate
+// arrives as (t_cut, i_cut); one that arrives one place early (a retroactive S_2 cut) is
+// swapped in front of the last cut.  Every cut but the last is final, and the last is
+// final once it is at or before the scan's frontier.  Final cuts are converted in place,
+// in order, into (last frame of the span, value of the span), so that writing a frame row
+// costs one comparison per lane and a new span two shared-memory loads.  The pixel's last
+// record is TAIL: it holds the last value for the frames after the last spike (0 if there
+// is no span).
 constexpr int TAIL = INT_MAX;
 
 template <typename OutT>
 struct FrameSink {
-    int *rt;       // &rec_t[warp][0][lane], slot stride 32
-    int *ri;
+    int *rt;       // &rec_t[warp][0][lane], slot stride 32: t_cut, or the last frame once converted
+    int *ri;       // i_cut, or the value's bits once converted
     OutT *col;     // out + p: frame k at col[k * P]
     int64_t P;
     float theta;
@@ -204,34 +207,28 @@ struct FrameSink {
     int T_out;
     int head, tail;  // ring positions (monotone)
     int sorted;      // records before this position are in time order
+    int conv;        // records before this position are converted
     int W;           // frames < W are written
+    int kf;          // frames < kf are covered by converted records
     int bad;         // set if a flush found no record for a frame (never expected)
-    // cursor: the record at head spans (cur_ts, cur_te] with value cur_v; (cur_ts, cur_ti)
-    // is the previous cut (the first spike and -1 before the first record)
-    int cur_ts, cur_ti, cur_te, cur_ie;
+    int ct, ci;      // the last converted cut (the first spike and -1 before the first)
+    float cv;        // value of the last converted span (0 before the first)
+    int cur_ke;      // cursor: the record at head covers frames up to cur_ke, value cur_v
     float cur_v;
 
     __device__ __forceinline__ int slot(int j) const { return (j & (QCAP - 1)) * 32; }
     __device__ __forceinline__ int frame_of(int t) const {  // t / stride, t >= 0
         return stride == 1 ? t : static_cast<int>(__umulhi(static_cast<uint32_t>(t), div_m) >> div_s);
     }
-    __device__ __forceinline__ void store(int k, float v) { col[static_cast<int64_t>(k) * P] = to_out<OutT>(v); }
-
     __device__ __forceinline__ void load() {
         const int s = slot(head);
-        cur_te = rt[s];
-        cur_ie = ri[s];
-        if (cur_te != TAIL) cur_v = seq_value(theta, cur_ie - cur_ti, cur_te - cur_ts);
+        cur_ke = rt[s];
+        cur_v = __int_as_float(ri[s]);
     }
-    __device__ __forceinline__ void advance() {
-        cur_ts = cur_te;
-        cur_ti = cur_ie;
-        ++head;
-        load();
-    }
-    // A candidate that arrived one place early is swapped in front of its predecessor.
+    // A candidate that arrived one place early is swapped in front of its predecessor
+    // (converted records are final and never move).
     __device__ __forceinline__ void sort_new() {
-        for (int j = max(sorted - 1, head); j + 1 < tail; ++j) {
+        for (int j = max(sorted - 1, conv); j + 1 < tail; ++j) {
             const int a = slot(j), b = slot(j + 1);
             const int ta = rt[a], tb = rt[b];
             if (tb < ta) {
@@ -244,34 +241,41 @@ struct FrameSink {
         }
         sorted = tail;
     }
-    // frames with t_k at or before the last final cut are resolved (records sorted; the
-    // last record may be pending, the one before it is final)
-    __device__ __forceinline__ int resolved(int frontier) const {
-        if (tail == head) return W;
-        int ft = rt[slot(tail - 1)];
-        if (ft > frontier) ft = tail - 1 > head ? rt[slot(tail - 2)] : -1;
-        if (ft == TAIL) return T_out;
-        return ft < 0 ? W : max(W, frame_of(ft) + 1);
-    }
-    // write frame k, advancing over records that end before t_k
-    __device__ __forceinline__ void write_frame(int k) {
-        const int tk = k * stride;
-        while (tk > cur_te) {
-            if (head + 1 >= tail) {  // no record covers t_k: inconsistent, never expected
-                bad = 1;
-                return;
+    // records [conv, R) are final and sorted: (t_cut, i_cut) -> (last frame, value)
+    __device__ __forceinline__ void convert(int R) {
+        for (; conv < R; ++conv) {
+            const int s = slot(conv);
+            const int t = rt[s];
+            int ke;
+            if (t == TAIL) {
+                ke = T_out - 1;
+            } else {
+                const int i = ri[s];
+                cv = seq_value(theta, i - ci, t - ct);
+                ct = t;
+                ci = i;
+                ke = frame_of(t);
             }
-            advance();
+            rt[s] = ke;
+            ri[s] = __float_as_int(cv);
+            kf = max(kf, ke + 1);
         }
-        store(k, cur_v);
     }
-    __device__ __forceinline__ void drain_one() {  // ring full: write the oldest (final) record alone
+    // convert every final record: all but the last, and the last if it is at or before
+    // the frontier
+    __device__ __forceinline__ void convert_final(int frontier) {
+        int R = tail;
+        if (R > conv && rt[slot(R - 1)] > frontier) --R;
+        convert(R);
+    }
+    __device__ __forceinline__ void drain_one() {  // ring full: write the oldest record alone
         sort_new();
+        convert(head + 2);  // the ring holds QCAP records, so these two are final
         load();
-        const int kl = frame_of(cur_te);
-        for (int k = W; k <= kl; ++k) store(k, cur_v);
+        const int kl = min(cur_ke, T_out - 1);
+        for (int k = W; k <= kl; ++k) col[static_cast<int64_t>(k) * P] = to_out<OutT>(cur_v);
         if (kl + 1 > W) W = kl + 1;
-        advance();
+        ++head;
     }
     __device__ __forceinline__ void cand(int t, int i) {
         if (tail - head == QCAP) drain_one();
@@ -328,8 +332,11 @@ struct SegSink {
 // every lane up to its own resolved count.
 template <typename OutT>
 __device__ __forceinline__ void flush_rows(FrameSink<OutT> &sk, int frontier, bool valid, bool final_flush) {
-    if (valid && sk.sorted < sk.tail) sk.sort_new();
-    const int F = valid ? sk.resolved(frontier) : INT_MAX;
+    if (valid) {
+        if (sk.sorted < sk.tail) sk.sort_new();
+        sk.convert_final(frontier);
+    }
+    const int F = valid ? max(sk.W, sk.kf) : INT_MAX;
     const int Wl = valid ? sk.W : INT_MAX;
     const int used = valid ? sk.tail - sk.head : 0;
     const int Fmin = __reduce_min_sync(FULL, F);
@@ -344,10 +351,24 @@ __device__ __forceinline__ void flush_rows(FrameSink<OutT> &sk, int frontier, bo
         lim = Fmin;
     }
     if (Wmin >= khi) return;  // nothing to write (warp-uniform)
-    if (valid && sk.W < lim) sk.load();
-    for (int k = Wmin; k < khi; ++k)
-        if (valid && k >= sk.W && k < lim) sk.write_frame(k);
-    if (valid && lim > sk.W) sk.W = lim;
+    const int klo = valid ? sk.W : INT_MAX;
+    if (!valid) lim = 0;
+    if (sk.W < lim) sk.load();
+    OutT *ptr = sk.col + static_cast<int64_t>(Wmin) * sk.P;
+    for (int k = Wmin; k < khi; ++k, ptr += sk.P) {
+        if (k >= klo && k < lim) {
+            while (k > sk.cur_ke) {  // the next converted record
+                if (sk.head + 1 >= sk.conv) {  // none covers frame k: inconsistent, never expected
+                    sk.bad = 1;
+                    break;
+                }
+                ++sk.head;
+                sk.load();
+            }
+            *ptr = to_out<OutT>(sk.cur_v);
+        }
+    }
+    if (lim > sk.W) sk.W = lim;
 }
 
 // ------------------------------------------------------------------- the kernel ----
@@ -369,9 +390,9 @@ __device__ __forceinline__ void carry_load(const int *c, int64_t P, int64_t p, s
     sc.tq1 = c[9 * P];
     sc.dlo1 = c[10 * P];
     sc.dhi1 = c[11 * P];
-    fs.W = c[12 * P];
-    fs.cur_ts = fs.cur_te = c[13 * P];
-    fs.cur_ti = fs.cur_ie = c[14 * P];
+    fs.W = fs.kf = c[12 * P];
+    fs.ct = c[13 * P];
+    fs.ci = c[14 * P];
     const int npend = c[15 * P];
     if (npend > 0) {
         fs.rt[fs.slot(0)] = c[16 * P];
@@ -401,8 +422,8 @@ __device__ __forceinline__ void carry_store(int *c, int64_t P, int64_t p, const 
     c[10 * P] = sc.dlo1;
     c[11 * P] = sc.dhi1;
     c[12 * P] = fs.W;
-    c[13 * P] = fs.cur_ts;
-    c[14 * P] = fs.cur_ti;
+    c[13 * P] = fs.ct;
+    c[14 * P] = fs.ci;
     c[15 * P] = npend;
     c[16 * P] = npend > 0 ? fs.rt[fs.slot(pj)] : 0;
     c[17 * P] = npend > 0 ? fs.ri[fs.slot(pj)] : 0;
@@ -474,10 +495,10 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         fs.T_out = job.T_out;
         fs.div_m = job.div_m;
         fs.div_s = job.div_s;
-        fs.head = fs.tail = fs.sorted = fs.W = fs.bad = 0;
-        fs.cur_ts = fs.cur_te = 0;
-        fs.cur_ti = fs.cur_ie = -1;
-        fs.cur_v = 0.f;
+        fs.head = fs.tail = fs.sorted = fs.conv = fs.W = fs.kf = fs.bad = 0;
+        fs.ct = fs.cur_ke = 0;
+        fs.ci = -1;
+        fs.cv = fs.cur_v = 0.f;
         if (!(job.flags & JOB_FIRST) && valid) carry_load(job.carry, job.P, p, sc, fs);
     }
 
@@ -504,7 +525,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
                 const int t0 = base + __ffs(w) - 1;
                 sc.first_spike(t0);
                 if constexpr (SEGMENTS) ss.ct = t0;  // the first span starts here
-                else fs.cur_ts = t0;
+                else fs.ct = t0;
                 w &= w - 1;
             }
             if (w == 0xffffffffu && sc.absorb_ones(base)) w = 0;  // steady run of 1-intervals
@@ -529,22 +550,13 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         flush_rows(fs, INT_MAX, valid, true);
         if (valid && fs.bad) atomicOr(prm.status, DEV_INTERNAL);
     } else {
-        // piece end: write every resolved frame, fold the final cuts into the start of the
-        // open span, keep the pending candidates
-        if (valid) fs.sort_new();
-        const int S = sc.frontier();
-        flush_rows(fs, S, valid, true);
-        int j = fs.head;
+        // piece end: convert the final cuts and write every resolved frame; the last
+        // converted cut starts the open span, the rest are pending candidates
+        flush_rows(fs, sc.frontier(), valid, true);
         if (valid) {
-            for (; j < fs.tail; ++j) {
-                const int t = fs.rt[fs.slot(j)];
-                if (t > S) break;
-                fs.cur_ts = t;
-                fs.cur_ti = fs.ri[fs.slot(j)];
-            }
-            const int npend = fs.tail - j;
+            const int npend = fs.tail - fs.conv;
             if (npend > 2 || fs.bad) atomicOr(prm.status, DEV_INTERNAL);
-            carry_store(job.carry, job.P, p, sc, fs, npend > 2 ? 2 : npend, j);
+            carry_store(job.carry, job.P, p, sc, fs, npend > 2 ? 2 : npend, fs.conv);
         }
     }
     if constexpr (!SEGMENTS) {

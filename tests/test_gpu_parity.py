@@ -194,3 +194,20 @@ def test_large_1000x1000x20000_sampled(torch_cuda):
     R.close()
     _check_segments(seg, r, len(pix))
     _check_frames(f_s, r.frames, "f16")
+
+
+@pytest.mark.parametrize("order,stride,dtype", [(1, 1, "f32"), (2, 1, "f16"), (2, 7, "f32"), (1, 3, "f16")])
+def test_record_ring_overflow(torch_cuda, order, stride, dtype):
+    """One lane per warp never cuts (a constant interval of 4) and holds back the warp's
+    full rows, while the other lanes cut at every interval (1, 3, 1, 3, ...): their record
+    rings fill within a few words and write their oldest records alone."""
+    T, W = 3000, 80
+    bits = np.zeros((T, W), dtype=np.uint8)
+    t = np.arange(T)
+    for p in range(W):
+        if p % 32 == 5:
+            bits[t % 4 == p % 4, p] = 1
+        else:
+            bits[(t % 4 == 0) | (t % 4 == 1), p] = 1     # intervals 1, 3, 1, 3, ...
+            bits[: p % 11, p] = 0                         # stagger the lanes
+    _case(torch_cuda, spkgen.pack(bits), 1, W, T, order, stride, dtype)
