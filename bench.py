@@ -53,7 +53,8 @@ def parse_args(argv=None):
                          "refine: train the learned refiner on simulated clips, then evaluate it")
     ap.add_argument("--no-refiner", action="store_true",
                     help="single mode: skip the refiner evaluation on the headline stream")
-    ap.add_argument("--refine-clips", type=int, default=200)
+    ap.add_argument("--refine-clips", type=int, default=200,
+                    help="refine mode: clips to train on from scratch (0: load the packaged checkpoint)")
     return ap.parse_args(argv)
 
 
@@ -463,10 +464,12 @@ def run_refine(args):
     base = spkgen.WORKLOADS["dynamic_250x400x20000"]
     rec = pkg.Reconstructor(order=2, stride=base.stride)
     ref = refiner.Refiner(seed=0)
+    if args.refine_clips == 0:           # evaluate (and time) the committed checkpoint
+        ref.load(refiner.CHECKPOINT)
     clip = base.resized(T=2000)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = refiner.train_on_simulator(ref, rec, clip, args.refine_clips, steps_per_clip=2, batch=16)
+    losses = refiner.train_on_simulator(ref, rec, clip, args.refine_clips, steps_per_clip=2, batch=16) or [None]
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     # the training step alone (features and clips excluded), timed with CUDA events
