@@ -472,7 +472,12 @@ def run_refine(args):
     losses = refiner.train_on_simulator(ref, rec, clip, args.refine_clips, steps_per_clip=2, batch=16) or [None]
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    # the training step alone (features and clips excluded), timed with CUDA events
+    res = refiner_eval(ref, rec, base)
+    # the training step alone (features and clips excluded), timed with CUDA events on a
+    # copy of the refiner (the timing steps must not move the evaluated weights)
+    ref.save(os.path.join(tempfile.gettempdir(), f"spk_refiner_{os.getpid()}.npy"))
+    ref.close()
+    ref = refiner.Refiner(seed=0)
     x0, plain, gt = refiner.simulator_clip(rec, clip.resized(seed=999))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(3):
@@ -483,7 +488,6 @@ def run_refine(args):
     e1.record(ref.stream)
     torch.cuda.synchronize()
     step_ms = e0.elapsed_time(e1) / 10
-    res = refiner_eval(ref, rec, base)
     line = {"mode": "refine", "metric": "refiner PSNR gain vs plain (dB) and throughput",
             "training": {"clips": args.refine_clips, "clip": f"{clip.H}x{clip.W}x{clip.T} stride {clip.stride}",
                          "steps": 2 * args.refine_clips, "batch_frames": 16, "seconds": dt,

@@ -23,6 +23,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -52,115 +53,173 @@ __device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint
 
 __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
+// four 8x8 bf16 matrices from shared memory; lane l gives the address of row l % 8 of
+// matrix l / 8 and receives, of each matrix, row l / 4, elements 2 (l % 4) and 2 (l % 4) + 1
+__device__ __forceinline__ void ldsm_x4(uint32_t *r, const bf16 *p) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
 // ------------------------------------------------------------------- convolution ----
 // Y[n][y][x][co] = act(sum_{tap, ci} X[n][y+ky-1][x+kx-1][ci] * Wt[tap][co][ci] + b[co])
 // MODE 0: bf16 out, ReLU;  MODE 1: bf16 out, no bias, times (mask > 0) (the dgrad of a
 // ReLU layer);  MODE 2: fp32 out of channel 0 plus resid (the last layer).
+//
+// Persistent: a block stages the weights once, then walks tasks of RY rows x 128 pixels
+// of one image.  Within a task the three input rows an output row needs sit in a ring of
+// four row buffers; while the 4 warps multiply row y, cp.async fills input row y + 2 (zero
+// fill outside the image), so the loads overlap the tensor-core work.
+constexpr int RY = 16;  // output rows per task
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int CI, int CO, int MODE>
 __global__ void __launch_bounds__(128) conv3x3_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ Wt,
                                                       const float *__restrict__ bias, void *Y,
                                                       const bf16 *__restrict__ mask, const float *__restrict__ resid,
-                                                      int H, int W) {
+                                                      int N, int H, int W) {
     constexpr int CP = CI + 8;  // padded channel stride (conflict-free fragment loads)
+    constexpr int CH = CI / 8;  // 16-byte chunks per pixel
     extern __shared__ __align__(16) unsigned char smraw[];
-    bf16(*halo)[MT + 2][CP] = reinterpret_cast<bf16(*)[MT + 2][CP]>(smraw);
-    bf16(*wsm)[CO][CP] = reinterpret_cast<bf16(*)[CO][CP]>(smraw + sizeof(bf16) * 3 * (MT + 2) * CP);
-    const int x0 = blockIdx.x * MT, y = blockIdx.y, n = blockIdx.z;
+    bf16(*ring)[MT + 2][CP] = reinterpret_cast<bf16(*)[MT + 2][CP]>(smraw);  // [4][130][CP]
+    bf16(*wsm)[CO][CP] = reinterpret_cast<bf16(*)[CO][CP]>(smraw + sizeof(bf16) * 4 * (MT + 2) * CP);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    // stage the halo: rows y-1..y+1, pixels x0-1..x0+128, CI channels (16-byte chunks)
-    constexpr int CH = CI / 8;
-    for (int c = tid; c < 3 * (MT + 2) * CH; c += 128) {
-        const int r = c / ((MT + 2) * CH), rem = c % ((MT + 2) * CH), xx = rem / CH, ch = rem % CH;
-        const int yy = y + r - 1, xg = x0 - 1 + xx;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (yy >= 0 && yy < H && xg >= 0 && xg < W)
-            v = *reinterpret_cast<const uint4 *>(X + ((static_cast<int64_t>(n) * H + yy) * W + xg) * CI + ch * 8);
-        *reinterpret_cast<uint4 *>(&halo[r][xx][ch * 8]) = v;
-    }
     for (int c = tid; c < 9 * CO * CH; c += 128) {
         const int tap = c / (CO * CH), rem = c % (CO * CH), co = rem / CH, ch = rem % CH;
-        *reinterpret_cast<uint4 *>(&wsm[tap][co][ch * 8]) =
-            *reinterpret_cast<const uint4 *>(Wt + (static_cast<int64_t>(tap) * CO + co) * CI + ch * 8);
+        cp_async16(&wsm[tap][co][ch * 8], Wt + (static_cast<int64_t>(tap) * CO + co) * CI + ch * 8, true);
     }
-    __syncthreads();
-
+    cp_async_commit();
+    const int nxs = (W + MT - 1) / MT, nys = (H + RY - 1) / RY;
+    const int64_t ntask = static_cast<int64_t>(N) * nxs * nys;
     constexpr int NT = CO / 8;
-    float acc[2][NT][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < NT; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
     const int m0 = warp * 32;
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
-#pragma unroll
-        for (int kc = 0; kc < CI / 16; ++kc) {
-            uint32_t a[2][4], b[NT][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r0 = m0 + i * 16 + g + kx;
-                a[i][0] = ld32(&halo[ky][r0][kc * 16 + 2 * t]);
-                a[i][1] = ld32(&halo[ky][r0 + 8][kc * 16 + 2 * t]);
-                a[i][2] = ld32(&halo[ky][r0][kc * 16 + 2 * t + 8]);
-                a[i][3] = ld32(&halo[ky][r0 + 8][kc * 16 + 2 * t + 8]);
+    for (int64_t task = blockIdx.x; task < ntask; task += gridDim.x) {
+        const int xs = static_cast<int>(task % nxs);
+        const int ys = static_cast<int>((task / nxs) % nys);
+        const int n = static_cast<int>(task / (static_cast<int64_t>(nxs) * nys));
+        const int x0 = xs * MT, y0 = ys * RY, y1 = min(H, y0 + RY);
+        // input row r of this image into ring slot r & 3 (zeros outside the image)
+        auto issue = [&](int r) {
+            if (r > y1) return;  // past the last row this task reads
+            for (int c = tid; c < (MT + 2) * CH; c += 128) {
+                const int xx = c / CH, ch = c % CH, xg = x0 - 1 + xx;
+                const bool ok = r >= 0 && r < H && xg >= 0 && xg < W;
+                const bf16 *src = ok ? X + ((static_cast<int64_t>(n) * H + r) * W + xg) * CI + ch * 8 : X;
+                cp_async16(&ring[r & 3][xx][ch * 8], src, ok);
             }
-#pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                b[j][0] = ld32(&wsm[tap][j * 8 + g][kc * 16 + 2 * t]);
-                b[j][1] = ld32(&wsm[tap][j * 8 + g][kc * 16 + 2 * t + 8]);
-            }
+        };
+        __syncthreads();  // the previous task's reads of the ring are done
+        issue(y0 - 1);
+        issue(y0);
+        issue(y0 + 1);
+        cp_async_commit();
+        for (int y = y0; y < y1; ++y) {
+            issue(y + 2);  // the next row's input, into the slot row y - 2 left
+            cp_async_commit();
+            cp_async_wait1();  // every group but the one just issued
+            __syncthreads();   // rows y - 1 .. y + 1 (and the weights) have landed for every thread
+            float acc[2][NT][4];
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
-                for (int j = 0; j < NT; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+                for (int j = 0; j < NT; ++j)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int ky = tap / 3, kx = tap % 3;
+                const int slot = (y + ky - 1) & 3;
+#pragma unroll
+                for (int kc = 0; kc < CI / 16; ++kc) {
+                    uint32_t a[2][4], b[NT][2];
+                    // A (pixels x channels): matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7),
+                    // (rows 0-7, k 8-15), (rows 8-15, k 8-15) = a0..a3 of m16n8k16
+                    const int mr = (lane & 7) + ((lane >> 3) & 1) * 8, mk = (lane >> 4) * 8;
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) ldsm_x4(a[i], &ring[slot][m0 + i * 16 + kx + mr][kc * 16 + mk]);
+                    // B (channels x out channels, stored [co][ci]): matrices (co 0-7, k 0-7),
+                    // (co 0-7, k 8-15), (co 8-15, k 0-7), (co 8-15, k 8-15) = b0, b1 of two n8 tiles
+                    const int nr = (lane & 7) + (lane >> 4) * 8, nk = ((lane >> 3) & 1) * 8;
+#pragma unroll
+                    for (int j = 0; j < NT; j += 2) {
+                        uint32_t q[4];
+                        ldsm_x4(q, &wsm[tap][j * 8 + nr][kc * 16 + nk]);
+                        b[j][0] = q[0];
+                        b[j][1] = q[1];
+                        b[j + 1][0] = q[2];
+                        b[j + 1][1] = q[3];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2; ++i)
+#pragma unroll
+                        for (int j = 0; j < NT; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+                }
+            }
+            // epilogue: rows g and g+8 of each m16 tile, columns 2t and 2t+1 of each n8 tile
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int x = x0 + m0 + i * 16 + g + hh * 8;
+                    if (x >= W) continue;
+                    const int64_t pix = (static_cast<int64_t>(n) * H + y) * W + x;
+                    if constexpr (MODE == 2) {
+                        if (t == 0) static_cast<float *>(Y)[pix] = acc[i][0][hh * 2] + bias[0] + resid[pix];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NT; ++j) {
+                            const int co = j * 8 + 2 * t;
+                            float v0 = acc[i][j][hh * 2], v1 = acc[i][j][hh * 2 + 1];
+                            if (MODE == 0) {
+                                v0 = fmaxf(v0 + bias[co], 0.f);
+                                v1 = fmaxf(v1 + bias[co + 1], 0.f);
+                            } else {
+                                const __nv_bfloat162 mk =
+                                    *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * CO + co);
+                                if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                                if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                            }
+                            *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(Y) + pix * CO + co) =
+                                __floats2bfloat162_rn(v0, v1);
+                        }
+                    }
+                }
+            __syncthreads();  // every warp is done with slot (y - 1) & 3 before row y + 3 refills it
         }
     }
-    // epilogue: rows g and g+8 of each m16 tile, columns 2t and 2t+1 of each n8 tile
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int x = x0 + m0 + i * 16 + g + hh * 8;
-            if (x >= W) continue;
-            const int64_t pix = (static_cast<int64_t>(n) * H + y) * W + x;
-            if constexpr (MODE == 2) {
-                if (t == 0) static_cast<float *>(Y)[pix] = acc[i][0][hh * 2] + bias[0] + resid[pix];
-            } else {
-#pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                const int co = j * 8 + 2 * t;
-                float v0 = acc[i][j][hh * 2], v1 = acc[i][j][hh * 2 + 1];
-                if (MODE == 0) {
-                    v0 = fmaxf(v0 + bias[co], 0.f);
-                    v1 = fmaxf(v1 + bias[co + 1], 0.f);
-                } else {
-                    const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * CO + co);
-                    if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-                }
-                *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(Y) + pix * CO + co) =
-                    __floats2bfloat162_rn(v0, v1);
-            }
-            }
-        }
+    cp_async_wait0();
 }
 
 template <int CI, int CO>
-constexpr size_t conv_smem() { return sizeof(bf16) * (3 * (MT + 2) + 9 * CO) * (CI + 8); }
+constexpr size_t conv_smem() { return sizeof(bf16) * (4 * (MT + 2) + 9 * CO) * (CI + 8); }
 
 template <int CI, int CO, int MODE>
-void conv(cudaStream_t s, dim3 grid, const bf16 *X, const bf16 *Wt, const float *bias, void *Y, const bf16 *mask,
-          const float *resid, int H, int W) {
-    static bool attr = false;  // dynamic shared memory above 48 KB: opt in once
-    if (!attr) {
+void conv(cudaStream_t s, int N, int H, int W, const bf16 *X, const bf16 *Wt, const float *bias, void *Y,
+          const bf16 *mask, const float *resid) {
+    static int blocks_per_sm = 0, sms = 0;  // dynamic shared memory above 48 KB: opt in once
+    if (!blocks_per_sm) {
         cudaFuncSetAttribute(conv3x3_kernel<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(conv_smem<CI, CO>()));
-        attr = true;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, conv3x3_kernel<CI, CO, MODE>, 128,
+                                                      conv_smem<CI, CO>());
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
-    conv3x3_kernel<CI, CO, MODE><<<grid, 128, conv_smem<CI, CO>(), s>>>(X, Wt, bias, Y, mask, resid, H, W);
+    const int64_t ntask = static_cast<int64_t>(N) * ((W + MT - 1) / MT) * ((H + RY - 1) / RY);
+    const int64_t grid = std::min<int64_t>(ntask, static_cast<int64_t>(blocks_per_sm) * sms);
+    conv3x3_kernel<CI, CO, MODE><<<static_cast<unsigned>(grid), 128, conv_smem<CI, CO>(), s>>>(X, Wt, bias, Y, mask,
+                                                                                                resid, N, H, W);
 }
 
 // dW[tap][co][ci] += sum_p X[p + tap][ci] * dZ[p][co],  dB[co] += sum_p dZ[p][co].
@@ -388,14 +447,12 @@ int ensure_buffers(spk_refiner *r, int64_t pixels, bool train) {
 // (the backward pass reads them), for inference two of them are used in turn
 int forward(spk_refiner *r, cudaStream_t s, const bf16 *x0, const float *plain, int N, int H, int W, float *out,
             bool keep) {
-    dim3 grid((W + MT - 1) / MT, H, N);
     auto act = [&](int l) { return r->act[keep ? l : (l & 1)]; };
-    conv<16, 32, 0>(s, grid, x0, r->wt[0], r->w + layer_off(0) + layer_w(0), act(0), nullptr, nullptr, H, W);
+    conv<16, 32, 0>(s, N, H, W, x0, r->wt[0], r->w + layer_off(0) + layer_w(0), act(0), nullptr, nullptr);
     for (int l = 1; l < NL - 1; ++l)
-        conv<32, 32, 0>(s, grid, act(l - 1), r->wt[l], r->w + layer_off(l) + layer_w(l), act(l), nullptr, nullptr,
-                        H, W);
-    conv<32, 16, 2>(s, grid, act(NL - 2), r->wt[NL - 1], r->w + layer_off(NL - 1) + layer_w(NL - 1), out, nullptr,
-                    plain, H, W);
+        conv<32, 32, 0>(s, N, H, W, act(l - 1), r->wt[l], r->w + layer_off(l) + layer_w(l), act(l), nullptr, nullptr);
+    conv<32, 16, 2>(s, N, H, W, act(NL - 2), r->wt[NL - 1], r->w + layer_off(NL - 1) + layer_w(NL - 1), out, nullptr,
+                    plain);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPK_OK : rfail(r, SPK_ERR_CUDA, "refiner forward: %s", cudaGetErrorString(e));
 }
@@ -536,21 +593,20 @@ int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const f
     cudaMemsetAsync(r->loss, 0, sizeof(float), s);
     bf16 *dz = r->grad[0], *dz2 = r->grad[1];
     mse_grad_kernel<<<512, 256, 0, s>>>(r->out, gt, P, 1.f / static_cast<float>(P), dz, r->loss);
-    const dim3 grid((W + MT - 1) / MT, H, N);
     const int segs = 8;
     const int64_t nseg = static_cast<int64_t>(N) * H * ((W + MT - 1) / MT);
     const int wblocks = static_cast<int>((nseg + segs - 1) / segs);
     // layer 4 (linear): weight gradient, then the gradient of act[3] through ReLU
     wgrad_kernel<32, 16><<<wblocks, 288, 0, s>>>(r->act[3], dz, r->g + layer_off(4),
                                                  r->g + layer_off(4) + layer_w(4), N, H, W, segs);
-    conv<16, 32, 1>(s, grid, dz, r->wd[4], nullptr, dz2, r->act[3], nullptr, H, W);
+    conv<16, 32, 1>(s, N, H, W, dz, r->wd[4], nullptr, dz2, r->act[3], nullptr);
     for (int l = 3; l >= 1; --l) {
         bf16 *tmp = dz;
         dz = dz2;
         dz2 = tmp;
         wgrad_kernel<32, 32><<<wblocks, 288, 0, s>>>(r->act[l - 1], dz, r->g + layer_off(l),
                                                      r->g + layer_off(l) + layer_w(l), N, H, W, segs);
-        conv<32, 32, 1>(s, grid, dz, r->wd[l], nullptr, dz2, r->act[l - 1], nullptr, H, W);
+        conv<32, 32, 1>(s, N, H, W, dz, r->wd[l], nullptr, dz2, r->act[l - 1], nullptr);
     }
     wgrad_kernel<16, 32><<<wblocks, 288, 0, s>>>(x, dz2, r->g + layer_off(0), r->g + layer_off(0) + layer_w(0), N, H,
                                                  W, segs);
