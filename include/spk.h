@@ -243,6 +243,12 @@ int spk_refiner_forward(spk_refiner *r, void *stream, const void *x0, const floa
 int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const float *plain,
                            const float *gt, int N, int H, int W, float lr, float *loss_host);
 
+/* Waits for `stream` (a cudaStream_t) and reports the refiner kernels' status: SPK_OK, or
+ * SPK_ERR_TIMEOUT if a convolution gave up its bounded wait for the tensor cores (the
+ * status is then cleared), SPK_ERR_CUDA on a CUDA error.  spk_refiner_train_step with a
+ * loss_host performs the same check. */
+int spk_refiner_synchronize(spk_refiner *r, void *stream);
+
 /* Diagnostic of the bounded device waits (no counterpart in the paper).  Every wait of
  * the kernels (the mbarrier waits of the stream pipeline) gives up after a bounded time
  * (about 2 s) instead of hanging, sets the timeout bit of the context's status word and

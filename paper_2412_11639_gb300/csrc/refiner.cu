@@ -15,6 +15,8 @@
 // pixels by all output channels with mma.m16n8k16 (bf16 in, fp32 accumulate), the nine
 // taps x input channels forming K.  The weight gradient is a GEMM over pixels (K = pixels),
 // one warp per tap.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -53,173 +55,434 @@ __device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint
 
 __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
-// four 8x8 bf16 matrices from shared memory; lane l gives the address of row l % 8 of
-// matrix l / 8 and receives, of each matrix, row l / 4, elements 2 (l % 4) and 2 (l % 4) + 1
-__device__ __forceinline__ void ldsm_x4(uint32_t *r, const bf16 *p) {
-    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
-}
+
 
 // ------------------------------------------------------------------- convolution ----
 // Y[n][y][x][co] = act(sum_{tap, ci} X[n][y+ky-1][x+kx-1][ci] * Wt[tap][co][ci] + b[co])
 // MODE 0: bf16 out, ReLU;  MODE 1: bf16 out, no bias, times (mask > 0) (the dgrad of a
 // ReLU layer);  MODE 2: fp32 out of channel 0 plus resid (the last layer).
 //
-// Persistent: a block stages the weights once, then walks tasks of RY rows x 128 pixels
-// of one image.  Within a task the three input rows an output row needs sit in a ring of
-// four row buffers; while the 4 warps multiply row y, cp.async fills input row y + 2 (zero
-// fill outside the image), so the loads overlap the tensor-core work.
+// Implicit GEMM on the 5th-generation tensor cores.  An output row segment of 128 pixels
+// is one M = 128 tile; N = CO; K = 9 taps x CI, issued as 9 x CI/16 tcgen05.mma (bf16 in,
+// fp32 accumulate in tensor memory) by one thread.  Both operands are K-major without
+// swizzle: 8-row x 16-byte core matrices.  The input halo row (130 pixels) is stored as
+// CI/8 planes of [pixel][8 channels], so the core-matrix row stride is 16 bytes and the
+// 8-row group stride (SBO) 128 bytes: the A operand of tap (ky, kx) is the same planes
+// seen from a start address kx * 16 bytes further.  Weights are stored per tap as
+// [chunk][co][8 channels] (B operand, N = co rows).
+//
+// Persistent and warp-specialised: a block stages the weights once, then walks tasks of
+// RY rows x 128 pixels of one image.  One thread loads halo rows with TMA into a ring of
+// RING row slots; one thread issues the MMAs of output row y as soon as rows y - 1 .. y + 1
+// have landed and an accumulator is free, and releases a row slot (tcgen05.commit onto its
+// mbarrier) after the last MMA that reads it; four warps read finished accumulators out of
+// tensor memory and write the output rows.  Loads, MMAs and the write-out of different rows
+// overlap.
 constexpr int RY = 16;  // output rows per task
+constexpr long long MMA_WAIT_CYCLES = 4000000000LL;  // ~2 s: bounded waits
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(128) conv3x3_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ Wt,
-                                                      const float *__restrict__ bias, void *Y,
-                                                      const bf16 *__restrict__ mask, const float *__restrict__ resid,
-                                                      int N, int H, int W) {
-    constexpr int CP = CI + 8;  // padded channel stride (conflict-free fragment loads)
-    constexpr int CH = CI / 8;  // 16-byte chunks per pixel
-    extern __shared__ __align__(16) unsigned char smraw[];
-    bf16(*ring)[MT + 2][CP] = reinterpret_cast<bf16(*)[MT + 2][CP]>(smraw);  // [4][130][CP]
-    bf16(*wsm)[CO][CP] = reinterpret_cast<bf16(*)[CO][CP]>(smraw + sizeof(bf16) * 4 * (MT + 2) * CP);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    for (int c = tid; c < 9 * CO * CH; c += 128) {
-        const int tap = c / (CO * CH), rem = c % (CO * CH), co = rem / CH, ch = rem % CH;
-        cp_async16(&wsm[tap][co][ch * 8], Wt + (static_cast<int64_t>(tap) * CO + co) * CI + ch * 8, true);
-    }
-    cp_async_commit();
-    const int nxs = (W + MT - 1) / MT, nys = (H + RY - 1) / RY;
-    const int64_t ntask = static_cast<int64_t>(N) * nxs * nys;
-    constexpr int NT = CO / 8;
-    const int m0 = warp * 32;
-    for (int64_t task = blockIdx.x; task < ntask; task += gridDim.x) {
-        const int xs = static_cast<int>(task % nxs);
-        const int ys = static_cast<int>((task / nxs) % nys);
-        const int n = static_cast<int>(task / (static_cast<int64_t>(nxs) * nys));
-        const int x0 = xs * MT, y0 = ys * RY, y1 = min(H, y0 + RY);
-        // input row r of this image into ring slot r & 3 (zeros outside the image)
-        auto issue = [&](int r) {
-            if (r > y1) return;  // past the last row this task reads
-            for (int c = tid; c < (MT + 2) * CH; c += 128) {
-                const int xx = c / CH, ch = c % CH, xg = x0 - 1 + xx;
-                const bool ok = r >= 0 && r < H && xg >= 0 && xg < W;
-                const bf16 *src = ok ? X + ((static_cast<int64_t>(n) * H + r) * W + xg) * CI + ch * 8 : X;
-                cp_async16(&ring[r & 3][xx][ch * 8], src, ok);
-            }
-        };
-        __syncthreads();  // the previous task's reads of the ring are done
-        issue(y0 - 1);
-        issue(y0);
-        issue(y0 + 1);
-        cp_async_commit();
-        for (int y = y0; y < y1; ++y) {
-            issue(y + 2);  // the next row's input, into the slot row y - 2 left
-            cp_async_commit();
-            cp_async_wait1();  // every group but the one just issued
-            __syncthreads();   // rows y - 1 .. y + 1 (and the weights) have landed for every thread
-            float acc[2][NT][4];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < NT; ++j)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int ky = tap / 3, kx = tap % 3;
-                const int slot = (y + ky - 1) & 3;
-#pragma unroll
-                for (int kc = 0; kc < CI / 16; ++kc) {
-                    uint32_t a[2][4], b[NT][2];
-                    // A (pixels x channels): matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7),
-                    // (rows 0-7, k 8-15), (rows 8-15, k 8-15) = a0..a3 of m16n8k16
-                    const int mr = (lane & 7) + ((lane >> 3) & 1) * 8, mk = (lane >> 4) * 8;
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) ldsm_x4(a[i], &ring[slot][m0 + i * 16 + kx + mr][kc * 16 + mk]);
-                    // B (channels x out channels, stored [co][ci]): matrices (co 0-7, k 0-7),
-                    // (co 0-7, k 8-15), (co 8-15, k 0-7), (co 8-15, k 8-15) = b0, b1 of two n8 tiles
-                    const int nr = (lane & 7) + (lane >> 4) * 8, nk = ((lane >> 3) & 1) * 8;
-#pragma unroll
-                    for (int j = 0; j < NT; j += 2) {
-                        uint32_t q[4];
-                        ldsm_x4(q, &wsm[tap][j * 8 + nr][kc * 16 + nk]);
-                        b[j][0] = q[0];
-                        b[j][1] = q[1];
-                        b[j + 1][0] = q[2];
-                        b[j + 1][1] = q[3];
-                    }
-#pragma unroll
-                    for (int i = 0; i < 2; ++i)
-#pragma unroll
-                        for (int j = 0; j < NT; ++j) mma_bf16(acc[i][j], a[i], b[j]);
-                }
-            }
-            // epilogue: rows g and g+8 of each m16 tile, columns 2t and 2t+1 of each n8 tile
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int x = x0 + m0 + i * 16 + g + hh * 8;
-                    if (x >= W) continue;
-                    const int64_t pix = (static_cast<int64_t>(n) * H + y) * W + x;
-                    if constexpr (MODE == 2) {
-                        if (t == 0) static_cast<float *>(Y)[pix] = acc[i][0][hh * 2] + bias[0] + resid[pix];
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < NT; ++j) {
-                            const int co = j * 8 + 2 * t;
-                            float v0 = acc[i][j][hh * 2], v1 = acc[i][j][hh * 2 + 1];
-                            if (MODE == 0) {
-                                v0 = fmaxf(v0 + bias[co], 0.f);
-                                v1 = fmaxf(v1 + bias[co + 1], 0.f);
-                            } else {
-                                const __nv_bfloat162 mk =
-                                    *reinterpret_cast<const __nv_bfloat162 *>(mask + pix * CO + co);
-                                if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-                                if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-                            }
-                            *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(Y) + pix * CO + co) =
-                                __floats2bfloat162_rn(v0, v1);
-                        }
-                    }
-                }
-            __syncthreads();  // every warp is done with slot (y - 1) & 3 before row y + 3 refills it
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false (and the status word flagged) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > MMA_WAIT_CYCLES) {
+            atomicOr(status, 1);
+            return false;
         }
-    }
-    cp_async_wait0();
+    return true;
 }
 
+// shared-memory matrix descriptor: K-major, no swizzle; leading (K) and stride (M/N)
+// byte offsets between core matrices
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // descriptor version 1
+}
+// instruction descriptor of kind::f16: bf16 A and B, fp32 D, both K-major, M x N
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16_tc(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+// 32 lanes x 16 columns of fp32 accumulator: thread l of the warp gets lane (base + l)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+constexpr int RING = 5;  // input-row slots
+constexpr int NACC = 4;  // accumulators in tensor memory
+
 template <int CI, int CO>
-constexpr size_t conv_smem() { return sizeof(bf16) * (4 * (MT + 2) + 9 * CO) * (CI + 8); }
+struct ConvSmem {
+    static constexpr int CH = CI / 8;                        // 16-byte channel chunks
+    static constexpr int PLANE = 2176;                       // one chunk plane of a halo row: 130 x 16 B, 128-aligned
+    static constexpr int SLOT = CH * PLANE;                  // one halo row
+    static constexpr int WPLANE = CO * 16;                   // one chunk plane of a tap's weights
+    static constexpr int W_OFF = RING * SLOT;
+    static constexpr int STG_OFF = W_OFF + 9 * CH * WPLANE;  // output staging: 4 warps x 32 pixels x CO
+    static constexpr int BAR_OFF = STG_OFF + 4 * 32 * CO * 2;
+    // full[RING], empty[RING], acc_full[NACC], acc_empty[NACC], done, then the TMEM address
+    static constexpr int TMEM_OFF = BAR_OFF + 8 * (2 * RING + 2 * NACC + 1);
+    static constexpr int BYTES = TMEM_OFF + 16 + 128;        // + 128 to align the base
+    static constexpr int TCOLS = NACC * CO < 32 ? 32 : NACC * CO;
+};
+
+// Roles: warps 0-3 read accumulators out of tensor memory (warp w owns TMEM lanes 32w..)
+// and write the output rows; warp 4 (one thread) loads halo rows with TMA into the ring;
+// warp 5 (one thread) issues the MMAs, and allocates / frees the tensor memory.
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CUtensorMap xmap,
+                                                      const bf16 *__restrict__ Wt, const float *__restrict__ bias,
+                                                      void *Y, const bf16 *__restrict__ mask,
+                                                      const float *__restrict__ resid, int N, int H, int W,
+                                                      int *status) {
+    using L = ConvSmem<CI, CO>;
+    constexpr int CH = L::CH;
+    constexpr uint32_t IDESC = mma_idesc(MT, CO);
+    constexpr uint32_t ROW_TX = CH * (MT + 2) * 16;  // bytes of one halo row
+    extern __shared__ unsigned char smraw_[];
+    unsigned char *smraw = smraw_ + ((128 - (smem_u32(smraw_) & 127)) & 127);
+    const uint32_t sbase = smem_u32(smraw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smraw + L::BAR_OFF);
+    uint64_t *empty = full + RING;
+    uint64_t *accf = empty + RING;
+    uint64_t *acce = accf + NACC;
+    uint64_t *done = acce + NACC;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smraw + L::TMEM_OFF);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int i = 0; i < RING; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < NACC; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 4);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(L::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // weights: Wt[tap][co][ci] -> [tap][chunk][co][8]
+    for (int c = tid; c < 9 * CO * CH; c += 192) {
+        const int tap = c / (CO * CH), rem = c % (CO * CH), co = rem / CH, ch = rem % CH;
+        cp_async16(sbase + L::W_OFF + ((tap * CH + ch) * CO + co) * 16,
+                   Wt + (static_cast<int64_t>(tap) * CO + co) * CI + ch * 8, true);
+    }
+    cp_async_commit();
+    cp_async_wait0();
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int nxs = (W + MT - 1) / MT, nys = (H + RY - 1) / RY;
+    const int64_t ntask = static_cast<int64_t>(N) * nxs * nys;
+    auto geometry = [&](int64_t task, int &n, int &x0, int &y0, int &y1) {
+        const int xs = static_cast<int>(task % nxs);
+        const int ys = static_cast<int>((task / nxs) % nys);
+        n = static_cast<int>(task / (static_cast<int64_t>(nxs) * nys));
+        x0 = xs * MT;
+        y0 = ys * RY;
+        y1 = min(H, y0 + RY);
+    };
+
+    if (warp == 4) {  // ------------------------------------------------ TMA producer ----
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
+            int64_t q = 0;
+            bool ok = true;
+            for (int64_t task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+                int n, x0, y0, y1;
+                geometry(task, n, x0, y0, y1);
+                for (int r = y0 - 1; r <= y1; ++r, ++q) {
+                    const int sl = static_cast<int>(q % RING);
+                    if (q >= RING && !mbar_wait(&empty[sl], static_cast<uint32_t>((q / RING - 1) & 1), status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[sl], ROW_TX);
+                    for (int ch = 0; ch < CH; ++ch)
+                        tma_load_4d(sbase + sl * L::SLOT + ch * L::PLANE, &xmap, &full[sl], ch * 8, x0 - 1, r, n);
+                }
+            }
+            // let every issued copy land before this thread leaves
+            for (int64_t j = q > RING ? q - RING : 0; j < q; ++j)
+                if (!mbar_wait(&full[j % RING], static_cast<uint32_t>((j / RING) & 1), status)) break;
+        }
+    } else if (warp == 5) {  // ----------------------------------------- MMA issuer ----
+        if (lane == 0) {
+            int64_t q = 0, o = 0;
+            bool ok = true;
+            auto wait_full = [&](int64_t j) {
+                return mbar_wait(&full[j % RING], static_cast<uint32_t>((j / RING) & 1), status);
+            };
+            for (int64_t task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+                int n, x0, y0, y1;
+                geometry(task, n, x0, y0, y1);
+                const int64_t qb = q;  // the load of input row y0 - 1
+                if (!wait_full(qb) || !wait_full(qb + 1)) {
+                    ok = false;
+                    break;
+                }
+                for (int y = y0; y < y1; ++y, ++o) {
+                    const int64_t i = y - y0;
+                    const int a = static_cast<int>(o % NACC);
+                    if (!wait_full(qb + i + 2) ||
+                        (o >= NACC && !mbar_wait(&acce[a], static_cast<uint32_t>((o / NACC - 1) & 1), status))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + static_cast<uint32_t>(a * CO);
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ky = tap / 3, kx = tap % 3;
+                        const uint32_t arow =
+                            sbase + static_cast<uint32_t>((qb + i + ky) % RING) * L::SLOT + kx * 16;
+#pragma unroll
+                        for (int s = 0; s < CI / 16; ++s) {
+                            const uint64_t ad = smem_desc(arow + 2 * s * L::PLANE, L::PLANE, 128);
+                            const uint64_t bd =
+                                smem_desc(sbase + L::W_OFF + (tap * CH + 2 * s) * L::WPLANE, L::WPLANE, 128);
+                            mma_bf16_tc(d, ad, bd, IDESC, (tap | s) ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(&accf[a]);
+                    mma_commit(&empty[(qb + i) % RING]);  // input row y - 1 has no later reader
+                }
+                if (!ok) break;
+                const int64_t rows = y1 - y0;
+                mma_commit(&empty[(qb + rows) % RING]);      // input rows y1 - 1 and y1
+                mma_commit(&empty[(qb + rows + 1) % RING]);
+                q = qb + rows + 2;
+            }
+            mma_commit(done);  // every MMA of this block has completed once this arrives
+            mbar_wait(done, 0, status);
+        }
+    } else {  // ------------------------------------------------------- epilogue warps ----
+        constexpr int CPP = CO / 8;  // 16-byte chunks per pixel
+        float bv[MODE == 0 ? CO : 1];  // the bias stays in registers (Y may alias it as far as the compiler knows)
+        if constexpr (MODE == 0) {
+#pragma unroll
+            for (int c = 0; c < CO; ++c) bv[c] = bias[c];
+        } else if constexpr (MODE == 2) {
+            bv[0] = bias[0];
+        }
+        uint4 *stg = reinterpret_cast<uint4 *>(smraw + L::STG_OFF) + warp * 32 * CPP;
+        // chunk swizzle of pixel p: the 8 lanes of a 128-byte wavefront hit 8 distinct bank groups
+        auto swz = [](int p) { return (p / (8 / CPP)) & (CPP - 1); };
+        int64_t o = 0;
+        bool ok = true;
+        for (int64_t task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+            int n, x0, y0, y1;
+            geometry(task, n, x0, y0, y1);
+            const int xw = x0 + warp * 32;  // this warp's first pixel
+            for (int y = y0; y < y1; ++y, ++o) {
+                const int a = static_cast<int>(o % NACC);
+                const int x = xw + lane;
+                const int64_t row = (static_cast<int64_t>(n) * H + y) * W;
+                // loads that do not depend on the MMAs go out before the wait
+                uint4 mk[MODE == 1 ? CPP : 1];
+                float rs = 0.f;
+                if (x < W) {
+                    if constexpr (MODE == 1) {
+#pragma unroll
+                        for (int qd = 0; qd < CPP; ++qd) mk[qd] = reinterpret_cast<const uint4 *>(mask + (row + x) * CO)[qd];
+                    } else if constexpr (MODE == 2) {
+                        rs = resid[row + x];
+                    }
+                }
+                if (!__all_sync(0xffffffffu, mbar_wait(&accf[a], static_cast<uint32_t>((o / NACC) & 1), status))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t ta = tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(a * CO);
+                float v[CO];
+#pragma unroll
+                for (int c = 0; c < CO; c += 16) tmem_ld16(ta + c, v + c);
+                tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[a]);  // the accumulator may be overwritten
+                if constexpr (MODE == 2) {
+                    if (x < W) static_cast<float *>(Y)[row + x] = v[0] + bv[0] + rs;
+                } else {
+                    // the warp's 32 pixels x CO channels are contiguous in Y: stage them in shared
+                    // memory and write them out as whole 512-byte runs
+#pragma unroll
+                    for (int qd = 0; qd < CPP; ++qd) {
+                        float w8[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) w8[e] = v[qd * 8 + e];
+                        if constexpr (MODE == 0) {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) w8[e] = fmaxf(w8[e] + bv[qd * 8 + e], 0.f);
+                        } else {
+                            const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&mk[qd]);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                if (!(__bfloat162float(m2[e].x) > 0.f)) w8[2 * e] = 0.f;
+                                if (!(__bfloat162float(m2[e].y) > 0.f)) w8[2 * e + 1] = 0.f;
+                            }
+                        }
+                        uint4 ov;
+                        __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(&ov);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) o2[e] = __floats2bfloat162_rn(w8[2 * e], w8[2 * e + 1]);
+                        stg[lane * CPP + (qd ^ swz(lane))] = ov;
+                    }
+                    __syncwarp();
+                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<bf16 *>(Y) + (row + xw) * CO);
+#pragma unroll
+                    for (int k = 0; k < CPP; ++k) {
+                        const int c = k * 32 + lane, px = c / CPP, ch = c % CPP;  // chunk c of the warp's run
+                        if (xw + px < W) dst[c] = stg[px * CPP + (ch ^ swz(px))];
+                    }
+                    __syncwarp();  // the staging is read before the next row overwrites it
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TCOLS) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// halo-row loads of an NHWC bf16 tensor: box of 8 channels x 130 pixels x 1 row x 1 image
+bool make_xmap(CUtensorMap *map, const bf16 *X, int C, int N, int H, int W) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[4] = {static_cast<cuuint64_t>(C), static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H),
+                          static_cast<cuuint64_t>(N)};
+    cuuint64_t strides[3] = {static_cast<cuuint64_t>(C) * 2, static_cast<cuuint64_t>(W) * C * 2,
+                             static_cast<cuuint64_t>(H) * W * C * 2};
+    cuuint32_t box[4] = {8, MT + 2, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(X), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 template <int CI, int CO, int MODE>
-void conv(cudaStream_t s, int N, int H, int W, const bf16 *X, const bf16 *Wt, const float *bias, void *Y,
-          const bf16 *mask, const float *resid) {
-    static int blocks_per_sm = 0, sms = 0;  // dynamic shared memory above 48 KB: opt in once
+bool conv(cudaStream_t s, int *status, int N, int H, int W, const bf16 *X, const bf16 *Wt, const float *bias,
+          void *Y, const bf16 *mask, const float *resid) {
+    constexpr int bytes = ConvSmem<CI, CO>::BYTES;
+    static int blocks_per_sm = 0, sms = 0;  // attributes and occupancy: once
     if (!blocks_per_sm) {
-        cudaFuncSetAttribute(conv3x3_kernel<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(conv_smem<CI, CO>()));
-        int dev = 0;
+        cudaFuncSetAttribute(conv3x3_kernel<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        int dev = 0, smem_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, conv3x3_kernel<CI, CO, MODE>, 128,
-                                                      conv_smem<CI, CO>());
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, conv3x3_kernel<CI, CO, MODE>);
+        // resident blocks: shared memory (1 KB reserved per block), registers (allocated per
+        // warp in units of 256), and the 512 tensor-memory columns, TCOLS per block
+        const int by_smem = smem_sm / (bytes + 1024);
+        const int regs_warp = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;
+        const int by_regs = 65536 / (regs_warp * 6);
+        blocks_per_sm = std::max(1, std::min({by_smem, by_regs, 512 / ConvSmem<CI, CO>::TCOLS}));
     }
+    CUtensorMap map;
+    if (!make_xmap(&map, X, CI, N, H, W)) return false;
     const int64_t ntask = static_cast<int64_t>(N) * ((W + MT - 1) / MT) * ((H + RY - 1) / RY);
     const int64_t grid = std::min<int64_t>(ntask, static_cast<int64_t>(blocks_per_sm) * sms);
-    conv3x3_kernel<CI, CO, MODE><<<static_cast<unsigned>(grid), 128, conv_smem<CI, CO>(), s>>>(X, Wt, bias, Y, mask,
-                                                                                                resid, N, H, W);
+    conv3x3_kernel<CI, CO, MODE><<<static_cast<unsigned>(grid), 192, bytes, s>>>(map, Wt, bias, Y, mask, resid, N, H,
+                                                                                  W, status);
+    return true;
 }
 
 // dW[tap][co][ci] += sum_p X[p + tap][ci] * dZ[p][co],  dB[co] += sum_p dZ[p][co].
@@ -376,6 +639,7 @@ struct spk_refiner {
     float *w, *m, *v, *g;      // fp32 parameters, Adam moments, gradient (NPARAM each)
     bf16 *wt[NL], *wd[NL];     // forward and dgrad weights
     float *loss;               // device scalar
+    int *status;               // device word: bit 0 set if a kernel gave up a bounded wait
     bf16 *act[NL];             // activations of layers 0..3 (act[4] unused) [N][H][W][32]
     bf16 *grad[2];             // two ping-pong gradient buffers [N][H][W][32]
     float *out;                // training forward output
@@ -448,11 +712,14 @@ int ensure_buffers(spk_refiner *r, int64_t pixels, bool train) {
 int forward(spk_refiner *r, cudaStream_t s, const bf16 *x0, const float *plain, int N, int H, int W, float *out,
             bool keep) {
     auto act = [&](int l) { return r->act[keep ? l : (l & 1)]; };
-    conv<16, 32, 0>(s, N, H, W, x0, r->wt[0], r->w + layer_off(0) + layer_w(0), act(0), nullptr, nullptr);
+    bool ok = conv<16, 32, 0>(s, r->status, N, H, W, x0, r->wt[0], r->w + layer_off(0) + layer_w(0), act(0), nullptr,
+                              nullptr);
     for (int l = 1; l < NL - 1; ++l)
-        conv<32, 32, 0>(s, N, H, W, act(l - 1), r->wt[l], r->w + layer_off(l) + layer_w(l), act(l), nullptr, nullptr);
-    conv<32, 16, 2>(s, N, H, W, act(NL - 2), r->wt[NL - 1], r->w + layer_off(NL - 1) + layer_w(NL - 1), out, nullptr,
-                    plain);
+        ok = ok && conv<32, 32, 0>(s, r->status, N, H, W, act(l - 1), r->wt[l], r->w + layer_off(l) + layer_w(l),
+                                   act(l), nullptr, nullptr);
+    ok = ok && conv<32, 16, 2>(s, r->status, N, H, W, act(NL - 2), r->wt[NL - 1],
+                               r->w + layer_off(NL - 1) + layer_w(NL - 1), out, nullptr, plain);
+    if (!ok) return rfail(r, SPK_ERR_CUDA, "refiner forward: cuTensorMapEncodeTiled failed");
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPK_OK : rfail(r, SPK_ERR_CUDA, "refiner forward: %s", cudaGetErrorString(e));
 }
@@ -483,6 +750,7 @@ int spk_refiner_create(int device, uint64_t seed, spk_refiner **out) {
     bool ok = true;
     for (float **p : {&r->w, &r->m, &r->v, &r->g}) ok &= cudaMalloc(p, NPARAM * sizeof(float)) == cudaSuccess;
     ok &= cudaMalloc(&r->loss, sizeof(float)) == cudaSuccess;
+    ok &= cudaMalloc(&r->status, sizeof(int)) == cudaSuccess && cudaMemset(r->status, 0, sizeof(int)) == cudaSuccess;
     for (int l = 0; l < NL; ++l) {
         ok &= cudaMalloc(&r->wt[l], layer_w(l) * sizeof(bf16)) == cudaSuccess;
         ok &= cudaMalloc(&r->wd[l], layer_w(l) * sizeof(bf16)) == cudaSuccess;
@@ -524,6 +792,7 @@ int spk_refiner_destroy(spk_refiner *r) {
     cudaDeviceSynchronize();
     for (float *p : {r->w, r->m, r->v, r->g, r->loss, r->out})
         if (p) cudaFree(p);
+    if (r->status) cudaFree(r->status);
     for (int l = 0; l < NL; ++l) {
         if (r->wt[l]) cudaFree(r->wt[l]);
         if (r->wd[l]) cudaFree(r->wd[l]);
@@ -536,6 +805,21 @@ int spk_refiner_destroy(spk_refiner *r) {
 }
 
 const char *spk_refiner_last_error(const spk_refiner *r) { return r ? r->msg : g_ref_msg; }
+
+int spk_refiner_synchronize(spk_refiner *r, void *stream) {
+    if (!r) return SPK_ERR_ARG;
+    cudaSetDevice(r->device);
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return rfail(r, SPK_ERR_CUDA, "refiner: %s", cudaGetErrorString(cudaGetLastError()));
+    int st = 0;
+    if (cudaMemcpy(&st, r->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return rfail(r, SPK_ERR_CUDA, "refiner status read failed");
+    if (st) {
+        cudaMemset(r->status, 0, sizeof(int));
+        return rfail(r, SPK_ERR_TIMEOUT, "a refiner kernel gave up a bounded wait on the tensor cores");
+    }
+    return SPK_OK;
+}
 
 int spk_refiner_set_params(spk_refiner *r, const float *host, int64_t n) {
     if (!r || !host || n != NPARAM) return rfail(r, SPK_ERR_ARG, "need %lld parameters", (long long)NPARAM);
@@ -599,15 +883,16 @@ int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const f
     // layer 4 (linear): weight gradient, then the gradient of act[3] through ReLU
     wgrad_kernel<32, 16><<<wblocks, 288, 0, s>>>(r->act[3], dz, r->g + layer_off(4),
                                                  r->g + layer_off(4) + layer_w(4), N, H, W, segs);
-    conv<16, 32, 1>(s, N, H, W, dz, r->wd[4], nullptr, dz2, r->act[3], nullptr);
+    bool ok = conv<16, 32, 1>(s, r->status, N, H, W, dz, r->wd[4], nullptr, dz2, r->act[3], nullptr);
     for (int l = 3; l >= 1; --l) {
         bf16 *tmp = dz;
         dz = dz2;
         dz2 = tmp;
         wgrad_kernel<32, 32><<<wblocks, 288, 0, s>>>(r->act[l - 1], dz, r->g + layer_off(l),
                                                      r->g + layer_off(l) + layer_w(l), N, H, W, segs);
-        conv<32, 32, 1>(s, N, H, W, dz, r->wd[l], nullptr, dz2, r->act[l - 1], nullptr);
+        ok = ok && conv<32, 32, 1>(s, r->status, N, H, W, dz, r->wd[l], nullptr, dz2, r->act[l - 1], nullptr);
     }
+    if (!ok) return rfail(r, SPK_ERR_CUDA, "refiner backward: cuTensorMapEncodeTiled failed");
     wgrad_kernel<16, 32><<<wblocks, 288, 0, s>>>(x, dz2, r->g + layer_off(0), r->g + layer_off(0) + layer_w(0), N, H,
                                                  W, segs);
     r->steps += 1;
@@ -622,6 +907,7 @@ int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const f
             cudaStreamSynchronize(s) != cudaSuccess)
             return rfail(r, SPK_ERR_CUDA, "loss read failed");
         *loss_host /= static_cast<float>(P);
+        return spk_refiner_synchronize(r, stream);
     }
     return SPK_OK;
 }

@@ -23,7 +23,7 @@ EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reco
            "spk_get_tile", "spk_autotune", "spk_features", "spk_refiner_num_params",
            "spk_refiner_create", "spk_refiner_destroy", "spk_refiner_last_error",
            "spk_refiner_set_params", "spk_refiner_get_params", "spk_refiner_forward",
-           "spk_refiner_train_step")
+           "spk_refiner_train_step", "spk_refiner_synchronize")
 SPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -110,6 +110,8 @@ def load(path: str | None = None):
     lib.spk_refiner_forward.restype = i32
     lib.spk_refiner_train_step.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, f32, _c.POINTER(f32)]
     lib.spk_refiner_train_step.restype = i32
+    lib.spk_refiner_synchronize.argtypes = [vp, vp]
+    lib.spk_refiner_synchronize.restype = i32
     lib.spk_selftest_wait.argtypes = [vp, i64]
     lib.spk_selftest_wait.restype = i32
     lib.spk_reconstruct_host_noalloc.argtypes = [_c.POINTER(spk_config), vp, i32, i32, i32, f32, vp]
@@ -291,3 +293,7 @@ def spk_refiner_train_step(r, stream, x0, plain, gt, N, H, W, lr, want_loss=True
     _rcheck(r, load().spk_refiner_train_step(r, stream, _addr(x0), _addr(plain), _addr(gt), N, H, W, lr,
                                              _c.byref(loss) if want_loss else None))
     return loss.value
+
+
+def spk_refiner_synchronize(r, stream=None):
+    return _rcheck(r, load().spk_refiner_synchronize(r, stream))
