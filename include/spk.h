@@ -195,7 +195,9 @@ int64_t spk_launch_count(const spk_ctx *ctx);
  * squared error to a ground-truth intensity (Adam).  The plain frames remain the
  * fallback and the reference its error is judged against. */
 
-/* Refiner input for every frame of a stream: device bf16 [T_out][H][W][16] (NHWC).
+/* Refiner input for every frame of a stream: device bf16, 16 channels per pixel stored as
+ * two channel-chunk planes, [T_out][H][2][W][8] (channel c of pixel (y, x) of frame k at
+ * ((k*H + y)*2 + c/8)*W*8 + x*8 + c%8).
  * Channel 0 = plain[k][p] (device fp32 [T_out][H][W], e.g. the frames of spk_reconstruct
  * with SPK_F32); channels 4..7 = threshold / x for the last four intervals x completed at
  * or before t_k = k * stride (the most recent first, 0 where the pixel has fewer); the
@@ -230,7 +232,7 @@ int spk_refiner_set_params(spk_refiner *r, const float *host, int64_t n);
 int spk_refiner_get_params(spk_refiner *r, float *host, int64_t n, int which);
 
 /* out[n][y][x] = plain + network(x0) for N frames of H x W pixels.  x0: device bf16
- * [N][H][W][16] (spk_features), plain and out: device fp32 [N][H][W].  Runs on `stream`
+ * [N][H][2][W][8] (spk_features' layout), plain and out: device fp32 [N][H][W].  Runs on `stream`
  * (a cudaStream_t, NULL = legacy default); asynchronous.  N, H < 65536.
  * Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM. */
 int spk_refiner_forward(spk_refiner *r, void *stream, const void *x0, const float *plain, int N,

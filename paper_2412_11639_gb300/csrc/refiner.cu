@@ -3,8 +3,8 @@
 // The paper's method is parameter free (Sec. III-B); the refiner is this library's
 // extension: a 5-layer 3x3 convolutional network that takes, per pixel and frame, the plain
 // FSR/SSR value and the rates theta / x of the last four intervals (spk_features) and
-// predicts a correction to the plain value.  Layers (NHWC, bf16 activations, fp32
-// accumulation on the tensor cores):
+// predicts a correction to the plain value.  Layers (bf16 activations in channel-chunk
+// planes [N][H][C/8][W][8], fp32 accumulation on the tensor cores):
 //   L0 16 -> 32 (ReLU), L1..L3 32 -> 32 (ReLU), L4 32 -> 16 (linear; channel 0 is used,
 //   the other channels only pad K of the L4 gradient GEMM to the tensor-core k16)
 //   out = plain + L4(...)[channel 0]
@@ -55,6 +55,13 @@ __device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint
 
 __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
+// Activations with C channels are stored as channel-chunk planes, [N][H][C/8][W][8]: the 8
+// channels of a chunk are one 16-byte cell, and one image row of one chunk is W contiguous
+// cells.  Element (n, y, x, c):
+__host__ __device__ __forceinline__ int64_t act_idx(int n, int y, int x, int c, int H, int W, int C) {
+    return ((static_cast<int64_t>(n) * H + y) * (C / 8) + c / 8) * W * 8 + static_cast<int64_t>(x) * 8 + (c & 7);
+}
+
 
 
 // ------------------------------------------------------------------- convolution ----
@@ -72,7 +79,8 @@ __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_ca
 // [chunk][co][8 channels] (B operand, N = co rows).
 //
 // Persistent and warp-specialised: a block stages the weights once, then walks tasks of
-// RY rows x 128 pixels of one image.  One thread loads halo rows with TMA into a ring of
+// RY rows x 128 pixels of one image.  One thread loads halo rows with TMA (512-byte boxes of
+// the channel-chunk planes) into a ring of
 // RING row slots; one thread issues the MMAs of output row y as soon as rows y - 1 .. y + 1
 // have landed and an accumulator is free, and releases a row slot (tcgen05.commit onto its
 // mbarrier) after the last MMA that reads it; four warps read finished accumulators out of
@@ -168,27 +176,31 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                            int c2, int c3) {
+// 32 pixels x 8 channels of one chunk plane of one image row of a [N][H][C/8][W][8] tensor
+// seen as (W*8 elements, C/8, H, N): the element coordinate e (a multiple of 8, so 16-byte
+// aligned; negative or past the row for the halo: zero fill), chunk c, row y, image n
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int e, int c, int y,
+                                            int n) {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(e), "r"(c), "r"(y), "r"(n)
         : "memory");
 }
 
 constexpr int RING = 5;  // input-row slots
+constexpr int TMA_PX = 32;                  // pixels per TMA box (256 bf16: the largest box edge)
+constexpr int HALO_PX = 5 * TMA_PX;         // pixels loaded per halo row (>= 130)
 constexpr int NACC = 4;  // accumulators in tensor memory
 
 template <int CI, int CO>
 struct ConvSmem {
     static constexpr int CH = CI / 8;                        // 16-byte channel chunks
-    static constexpr int PLANE = 2176;                       // one chunk plane of a halo row: 130 x 16 B, 128-aligned
-    static constexpr int SLOT = CH * PLANE;                  // one halo row
+    static constexpr int PLANE = HALO_PX * 16;               // one chunk plane of a halo row: 160 x 16 B
+    static constexpr int SLOT = CH * PLANE;                  // one halo row (all planes)
     static constexpr int WPLANE = CO * 16;                   // one chunk plane of a tap's weights
     static constexpr int W_OFF = RING * SLOT;
-    static constexpr int STG_OFF = W_OFF + 9 * CH * WPLANE;  // output staging: 4 warps x 32 pixels x CO
-    static constexpr int BAR_OFF = STG_OFF + 4 * 32 * CO * 2;
+    static constexpr int BAR_OFF = W_OFF + 9 * CH * WPLANE;
     // full[RING], empty[RING], acc_full[NACC], acc_empty[NACC], done, then the TMEM address
     static constexpr int TMEM_OFF = BAR_OFF + 8 * (2 * RING + 2 * NACC + 1);
     static constexpr int BYTES = TMEM_OFF + 16 + 128;        // + 128 to align the base
@@ -207,7 +219,7 @@ __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CU
     using L = ConvSmem<CI, CO>;
     constexpr int CH = L::CH;
     constexpr uint32_t IDESC = mma_idesc(MT, CO);
-    constexpr uint32_t ROW_TX = CH * (MT + 2) * 16;  // bytes of one halo row
+    constexpr uint32_t ROW_TX = CH * HALO_PX * 16;  // bytes of one halo row
     extern __shared__ unsigned char smraw_[];
     unsigned char *smraw = smraw_ + ((128 - (smem_u32(smraw_) & 127)) & 127);
     const uint32_t sbase = smem_u32(smraw);
@@ -265,78 +277,92 @@ __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CU
     if (warp == 4) {  // ------------------------------------------------ TMA producer ----
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
-            int64_t q = 0;
+            int sl = 0, ph = 0, issued = 0;  // ring slot, its phase, loads issued
             bool ok = true;
             for (int64_t task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
                 int n, x0, y0, y1;
                 geometry(task, n, x0, y0, y1);
-                for (int r = y0 - 1; r <= y1; ++r, ++q) {
-                    const int sl = static_cast<int>(q % RING);
-                    if (q >= RING && !mbar_wait(&empty[sl], static_cast<uint32_t>((q / RING - 1) & 1), status)) {
+                for (int r = y0 - 1; r <= y1; ++r) {
+                    // the slot's previous row must have been released (from the second round on)
+                    if (issued >= RING && !mbar_wait(&empty[sl], ph ^ 1, status)) {
                         ok = false;
                         break;
                     }
                     mbar_expect_tx(&full[sl], ROW_TX);
                     for (int ch = 0; ch < CH; ++ch)
-                        tma_load_4d(sbase + sl * L::SLOT + ch * L::PLANE, &xmap, &full[sl], ch * 8, x0 - 1, r, n);
+                        for (int j = 0; j < HALO_PX / TMA_PX; ++j)
+                            tma_load_4d(sbase + sl * L::SLOT + ch * L::PLANE + j * TMA_PX * 16, &xmap, &full[sl],
+                                        (x0 - 1 + j * TMA_PX) * 8, ch, r, n);
+                    ++issued;
+                    if (++sl == RING) sl = 0, ph ^= 1;
                 }
             }
-            // let every issued copy land before this thread leaves
-            for (int64_t j = q > RING ? q - RING : 0; j < q; ++j)
-                if (!mbar_wait(&full[j % RING], static_cast<uint32_t>((j / RING) & 1), status)) break;
+            // let every issued copy land before this thread leaves: the last min(issued, RING) loads
+            for (int k = 0; k < RING && k < issued; ++k) {
+                if (--sl < 0) sl = RING - 1, ph ^= 1;
+                if (!mbar_wait(&full[sl], ph, status)) break;
+            }
         }
     } else if (warp == 5) {  // ----------------------------------------- MMA issuer ----
         if (lane == 0) {
-            int64_t q = 0, o = 0;
+            // descriptors are linear in the start address (bits 0-13 hold address / 16), so every
+            // operand is a base descriptor plus a compile-time or per-row offset
+            const uint64_t a_base = smem_desc(sbase, L::PLANE, 128);
+            const uint64_t b_base = smem_desc(sbase + L::W_OFF, L::WPLANE, 128);
+            int sl = 0, ph = 0;   // slot and phase of the next load to wait for
+            int a = 0, aph = 0;   // accumulator and its phase
+            int rows_done = 0;    // MMA rows issued (accumulator uses)
             bool ok = true;
-            auto wait_full = [&](int64_t j) {
-                return mbar_wait(&full[j % RING], static_cast<uint32_t>((j / RING) & 1), status);
+            auto wait_full = [&]() {  // the next load in order
+                const bool r = mbar_wait(&full[sl], ph, status);
+                if (++sl == RING) sl = 0, ph ^= 1;
+                return r;
             };
+            int s_first = 0;  // slot of input row y - 1 for the current output row
             for (int64_t task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
                 int n, x0, y0, y1;
                 geometry(task, n, x0, y0, y1);
-                const int64_t qb = q;  // the load of input row y0 - 1
-                if (!wait_full(qb) || !wait_full(qb + 1)) {
+                s_first = sl;
+                if (!wait_full() || !wait_full()) {  // input rows y0 - 1 and y0
                     ok = false;
                     break;
                 }
-                for (int y = y0; y < y1; ++y, ++o) {
-                    const int64_t i = y - y0;
-                    const int a = static_cast<int>(o % NACC);
-                    if (!wait_full(qb + i + 2) ||
-                        (o >= NACC && !mbar_wait(&acce[a], static_cast<uint32_t>((o / NACC - 1) & 1), status))) {
+                for (int y = y0; y < y1; ++y) {
+                    if (!wait_full() ||  // input row y + 1
+                        (rows_done >= NACC && !mbar_wait(&acce[a], aph ^ 1, status))) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t d = tmem + static_cast<uint32_t>(a * CO);
+                    uint64_t arow[3];
+                    for (int ky = 0, sk = s_first; ky < 3; ++ky, sk = (sk + 1 == RING ? 0 : sk + 1))
+                        arow[ky] = a_base + static_cast<uint64_t>((sk * L::SLOT) >> 4);
 #pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
-                        const int ky = tap / 3, kx = tap % 3;
-                        const uint32_t arow =
-                            sbase + static_cast<uint32_t>((qb + i + ky) % RING) * L::SLOT + kx * 16;
 #pragma unroll
                         for (int s = 0; s < CI / 16; ++s) {
-                            const uint64_t ad = smem_desc(arow + 2 * s * L::PLANE, L::PLANE, 128);
-                            const uint64_t bd =
-                                smem_desc(sbase + L::W_OFF + (tap * CH + 2 * s) * L::WPLANE, L::WPLANE, 128);
+                            const uint64_t ad = arow[tap / 3] + static_cast<uint64_t>(((tap % 3) * 16 + 2 * s * L::PLANE) >> 4);
+                            const uint64_t bd = b_base + static_cast<uint64_t>(((tap * CH + 2 * s) * L::WPLANE) >> 4);
                             mma_bf16_tc(d, ad, bd, IDESC, (tap | s) ? 1u : 0u);
                         }
                     }
                     mma_commit(&accf[a]);
-                    mma_commit(&empty[(qb + i) % RING]);  // input row y - 1 has no later reader
+                    mma_commit(&empty[s_first]);  // input row y - 1 has no later reader
+                    s_first = s_first + 1 == RING ? 0 : s_first + 1;
+                    ++rows_done;
+                    if (++a == NACC) a = 0, aph ^= 1;
                 }
                 if (!ok) break;
-                const int64_t rows = y1 - y0;
-                mma_commit(&empty[(qb + rows) % RING]);      // input rows y1 - 1 and y1
-                mma_commit(&empty[(qb + rows + 1) % RING]);
-                q = qb + rows + 2;
+                // input rows y1 - 1 and y1 are released after the task's last MMAs
+                mma_commit(&empty[s_first]);
+                mma_commit(&empty[s_first + 1 == RING ? 0 : s_first + 1]);
             }
             mma_commit(done);  // every MMA of this block has completed once this arrives
             mbar_wait(done, 0, status);
         }
     } else {  // ------------------------------------------------------- epilogue warps ----
-        constexpr int CPP = CO / 8;  // 16-byte chunks per pixel
+        constexpr int CPP = CO / 8;  // output chunks (planes)
         float bv[MODE == 0 ? CO : 1];  // the bias stays in registers (Y may alias it as far as the compiler knows)
         if constexpr (MODE == 0) {
 #pragma unroll
@@ -344,31 +370,28 @@ __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CU
         } else if constexpr (MODE == 2) {
             bv[0] = bias[0];
         }
-        uint4 *stg = reinterpret_cast<uint4 *>(smraw + L::STG_OFF) + warp * 32 * CPP;
-        // chunk swizzle of pixel p: the 8 lanes of a 128-byte wavefront hit 8 distinct bank groups
-        auto swz = [](int p) { return (p / (8 / CPP)) & (CPP - 1); };
-        int64_t o = 0;
+        int a = 0, aph = 0;  // accumulator and its phase
         bool ok = true;
         for (int64_t task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
             int n, x0, y0, y1;
             geometry(task, n, x0, y0, y1);
-            const int xw = x0 + warp * 32;  // this warp's first pixel
-            for (int y = y0; y < y1; ++y, ++o) {
-                const int a = static_cast<int>(o % NACC);
-                const int x = xw + lane;
-                const int64_t row = (static_cast<int64_t>(n) * H + y) * W;
-                // loads that do not depend on the MMAs go out before the wait
+            for (int y = y0; y < y1; ++y, a = (a + 1 == NACC ? 0 : a + 1), aph ^= (a == 0)) {
+                const int x = x0 + warp * 32 + lane;
+                // chunk q of pixel x of this row: cell (row * CPP + q) * W + x; loads that do not
+                // depend on the MMAs go out before the wait
+                const int64_t row = static_cast<int64_t>(n) * H + y;
                 uint4 mk[MODE == 1 ? CPP : 1];
                 float rs = 0.f;
                 if (x < W) {
                     if constexpr (MODE == 1) {
 #pragma unroll
-                        for (int qd = 0; qd < CPP; ++qd) mk[qd] = reinterpret_cast<const uint4 *>(mask + (row + x) * CO)[qd];
+                        for (int q = 0; q < CPP; ++q)
+                            mk[q] = reinterpret_cast<const uint4 *>(mask)[(row * CPP + q) * W + x];
                     } else if constexpr (MODE == 2) {
-                        rs = resid[row + x];
+                        rs = resid[row * W + x];
                     }
                 }
-                if (!__all_sync(0xffffffffu, mbar_wait(&accf[a], static_cast<uint32_t>((o / NACC) & 1), status))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&accf[a], aph, status))) {
                     ok = false;
                     break;
                 }
@@ -381,21 +404,20 @@ __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CU
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce[a]);  // the accumulator may be overwritten
+                if (x >= W) continue;
                 if constexpr (MODE == 2) {
-                    if (x < W) static_cast<float *>(Y)[row + x] = v[0] + bv[0] + rs;
+                    static_cast<float *>(Y)[row * W + x] = v[0] + bv[0] + rs;
                 } else {
-                    // the warp's 32 pixels x CO channels are contiguous in Y: stage them in shared
-                    // memory and write them out as whole 512-byte runs
 #pragma unroll
-                    for (int qd = 0; qd < CPP; ++qd) {
+                    for (int q = 0; q < CPP; ++q) {  // lanes write consecutive 16-byte cells of a plane
                         float w8[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) w8[e] = v[qd * 8 + e];
+                        for (int e = 0; e < 8; ++e) w8[e] = v[q * 8 + e];
                         if constexpr (MODE == 0) {
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) w8[e] = fmaxf(w8[e] + bv[qd * 8 + e], 0.f);
+                            for (int e = 0; e < 8; ++e) w8[e] = fmaxf(w8[e] + bv[q * 8 + e], 0.f);
                         } else {
-                            const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&mk[qd]);
+                            const __nv_bfloat162 *m2 = reinterpret_cast<const __nv_bfloat162 *>(&mk[q]);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 if (!(__bfloat162float(m2[e].x) > 0.f)) w8[2 * e] = 0.f;
@@ -406,16 +428,8 @@ __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CU
                         __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(&ov);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) o2[e] = __floats2bfloat162_rn(w8[2 * e], w8[2 * e + 1]);
-                        stg[lane * CPP + (qd ^ swz(lane))] = ov;
+                        reinterpret_cast<uint4 *>(Y)[(row * CPP + q) * W + x] = ov;
                     }
-                    __syncwarp();
-                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<bf16 *>(Y) + (row + xw) * CO);
-#pragma unroll
-                    for (int k = 0; k < CPP; ++k) {
-                        const int c = k * 32 + lane, px = c / CPP, ch = c % CPP;  // chunk c of the warp's run
-                        if (xw + px < W) dst[c] = stg[px * CPP + (ch ^ swz(px))];
-                    }
-                    __syncwarp();  // the staging is read before the next row overwrites it
                 }
             }
         }
@@ -441,15 +455,16 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-// halo-row loads of an NHWC bf16 tensor: box of 8 channels x 130 pixels x 1 row x 1 image
+// halo-row loads of a [N][H][C/8][W][8] bf16 tensor viewed as (W*8, C/8, H, N): boxes of
+// 256 elements (32 pixels) of one chunk plane, so every TMA request moves 512 contiguous bytes
 bool make_xmap(CUtensorMap *map, const bf16 *X, int C, int N, int H, int W) {
     auto enc = get_encode();
     if (!enc) return false;
-    cuuint64_t dims[4] = {static_cast<cuuint64_t>(C), static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H),
+    cuuint64_t dims[4] = {static_cast<cuuint64_t>(W) * 8, static_cast<cuuint64_t>(C / 8), static_cast<cuuint64_t>(H),
                           static_cast<cuuint64_t>(N)};
-    cuuint64_t strides[3] = {static_cast<cuuint64_t>(C) * 2, static_cast<cuuint64_t>(W) * C * 2,
+    cuuint64_t strides[3] = {static_cast<cuuint64_t>(W) * 16, static_cast<cuuint64_t>(W) * C * 2,
                              static_cast<cuuint64_t>(H) * W * C * 2};
-    cuuint32_t box[4] = {8, MT + 2, 1, 1};
+    cuuint32_t box[4] = {TMA_PX * 8, 1, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(X), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -518,13 +533,13 @@ __global__ void __launch_bounds__(288) wgrad_kernel(const bf16 *__restrict__ X, 
             const int r = c / ((MT + 2) * CI), rem = c % ((MT + 2) * CI), xx = rem / CI, ci = rem % CI;
             const int yy = y + r - 1, xg = x0 - 1 + xx;
             bf16 v = __float2bfloat16(0.f);
-            if (yy >= 0 && yy < H && xg >= 0 && xg < W) v = X[((static_cast<int64_t>(n) * H + yy) * W + xg) * CI + ci];
+            if (yy >= 0 && yy < H && xg >= 0 && xg < W) v = X[act_idx(n, yy, xg, ci, H, W, CI)];
             xt[r][ci][xx] = v;
         }
         for (int c = tid; c < MT * CO; c += 288) {
             const int xx = c / CO, co = c % CO, xg = x0 + xx;
             bf16 v = __float2bfloat16(0.f);
-            if (xg < W) v = dZ[((static_cast<int64_t>(n) * H + y) * W + xg) * CO + co];
+            if (xg < W) v = dZ[act_idx(n, y, xg, co, H, W, CO)];
             zt[co][xx] = v;
         }
         __syncthreads();
@@ -574,7 +589,8 @@ __global__ void __launch_bounds__(288) wgrad_kernel(const bf16 *__restrict__ X, 
 }
 
 // out - gt -> loss sum and dZ of the last layer (bf16, 16 channels, channel 0 only)
-__global__ void mse_grad_kernel(const float *out, const float *gt, int64_t n, float scale, bf16 *dz, float *loss) {
+__global__ void mse_grad_kernel(const float *out, const float *gt, int64_t n, int W, float scale, bf16 *dz,
+                                float *loss) {
     __shared__ float red[8];
     float s = 0.f;
     for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < n; i += 256LL * gridDim.x) {
@@ -583,8 +599,9 @@ __global__ void mse_grad_kernel(const float *out, const float *gt, int64_t n, fl
         uint4 v = make_uint4(0, 0, 0, 0);
         __nv_bfloat162 h = __floats2bfloat162_rn(2.f * d * scale, 0.f);
         v.x = *reinterpret_cast<uint32_t *>(&h);
-        reinterpret_cast<uint4 *>(dz + i * 16)[0] = v;
-        reinterpret_cast<uint4 *>(dz + i * 16)[1] = make_uint4(0, 0, 0, 0);
+        const int64_t row = i / W, x = i - row * W;  // dz: [N][H][2][W][8], channel 0 in plane 0
+        reinterpret_cast<uint4 *>(dz)[(row * 2) * W + x] = v;
+        reinterpret_cast<uint4 *>(dz)[(row * 2 + 1) * W + x] = make_uint4(0, 0, 0, 0);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -640,8 +657,8 @@ struct spk_refiner {
     bf16 *wt[NL], *wd[NL];     // forward and dgrad weights
     float *loss;               // device scalar
     int *status;               // device word: bit 0 set if a kernel gave up a bounded wait
-    bf16 *act[NL];             // activations of layers 0..3 (act[4] unused) [N][H][W][32]
-    bf16 *grad[2];             // two ping-pong gradient buffers [N][H][W][32]
+    bf16 *act[NL];             // activations of layers 0..3 (act[4] unused) [N][H][4][W][8]
+    bf16 *grad[2];             // two ping-pong gradient buffers, same layout
     float *out;                // training forward output
     int64_t cap;               // pixels the buffers hold
     int64_t steps;             // Adam steps taken
@@ -876,7 +893,7 @@ int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const f
     cudaMemsetAsync(r->g, 0, NPARAM * sizeof(float), s);
     cudaMemsetAsync(r->loss, 0, sizeof(float), s);
     bf16 *dz = r->grad[0], *dz2 = r->grad[1];
-    mse_grad_kernel<<<512, 256, 0, s>>>(r->out, gt, P, 1.f / static_cast<float>(P), dz, r->loss);
+    mse_grad_kernel<<<512, 256, 0, s>>>(r->out, gt, P, W, 1.f / static_cast<float>(P), dz, r->loss);
     const int segs = 8;
     const int64_t nseg = static_cast<int64_t>(N) * H * ((W + MT - 1) / MT);
     const int wblocks = static_cast<int>((nseg + segs - 1) / segs);

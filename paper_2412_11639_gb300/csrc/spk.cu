@@ -654,15 +654,16 @@ __global__ void __launch_bounds__(NTHREADS, 3) spk_tfp_kernel(const __grid_const
 }
 
 // --------------------------------------------------------- refiner input features ----
-// Input of the learned refiner, NHWC bf16 with 16 channels per pixel and frame: channel 0
-// the plain reconstruction of the frame (given, fp32), channels 4..7 theta / x for the last
-// four intervals x completed at or before t_k (the most recent first; 0 where the pixel
-// has fewer), every other channel 0.  Same TMA pipeline and transpose as the scan.
-constexpr int FEAT_C = 16;
+// Input of the learned refiner, bf16 with 16 channels per pixel and frame in two
+// channel-chunk planes, [T_out][H][2][W][8]: channel 0 the plain reconstruction of the frame
+// (given, fp32), channels 4..7 theta / x for the last four intervals x completed at or
+// before t_k (the most recent first; 0 where the pixel has fewer), every other channel 0.
+// Same TMA pipeline and transpose as the scan.
+constexpr int FEAT_C = 16;  // refiner input channels (two 8-channel planes)
 
 template <int TT>
 __global__ void __launch_bounds__(NTHREADS, 3)
-    spk_feature_kernel(const __grid_constant__ Batch<1> prm, const float *plain, __nv_bfloat16 *x0) {
+    spk_feature_kernel(const __grid_constant__ Batch<1> prm, const float *plain, __nv_bfloat16 *x0, int H, int W) {
     constexpr int WPT = TT / 32;
     extern __shared__ uint8_t smem_raw[];
     StageSmem<TT> &sm = *reinterpret_cast<StageSmem<TT> *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
@@ -695,6 +696,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     }
     const int64_t p = static_cast<int64_t>(blk) * BLOCK_PIX + warp * 32 + lane;
     const bool valid = p < job.P;
+    const int py = static_cast<int>(p / W), px = static_cast<int>(p - static_cast<int64_t>(py) * W);
     int last_t = -1, x1 = 0, x2 = 0, x3 = 0, x4 = 0;
     int k = 0;
     for (int j = 0; j < job.ntiles; ++j) {
@@ -739,9 +741,12 @@ __global__ void __launch_bounds__(NTHREADS, 3)
                     lo.y = 0u;
                     lo.z = *reinterpret_cast<uint32_t *>(&c45);
                     lo.w = *reinterpret_cast<uint32_t *>(&c67);
-                    uint4 *dst = reinterpret_cast<uint4 *>(x0 + q * FEAT_C);
-                    dst[0] = lo;
-                    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+                    // 16-byte cells: plane 0 of pixel (py, px) of frame k, then plane 1
+                    uint4 *cell = reinterpret_cast<uint4 *>(x0);
+                    const int64_t c0 = ((static_cast<int64_t>(k) * H + py) * 2) * W + px;
+                    cell[c0] = lo;
+                    cell[c0 + W] = make_uint4(0u, 0u, 0u, 0u);
+                    static_assert(FEAT_C == 16, "two planes of 8 channels");
                 }
             }
             while (w) {  // the rest of the word
@@ -1299,7 +1304,7 @@ int spk_features(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float
     prm.status = ctx->d_status;
     constexpr size_t bytes = sizeof(StageSmem<TT_DEFAULT>) + 128;
     spk_feature_kernel<TT_DEFAULT><<<nb, NTHREADS, bytes, ctx->stream>>>(prm, plain,
-                                                                          static_cast<__nv_bfloat16 *>(x0));
+                                                                          static_cast<__nv_bfloat16 *>(x0), H, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
     ++ctx->launches;

@@ -1,6 +1,6 @@
 """The learned refiner: Python handle over spk_refiner_* (the network runs in libspk).
 
-    x0 = features(rec, stream, H, W, T, plain)        # bf16 [T_out][H][W][16]
+    x0 = features(rec, stream, H, W, T, plain)        # bf16 [T_out][H][2][W][8]
     ref = Refiner(seed=0)
     loss = ref.train_step(x0, plain, gt, lr=1e-3)     # one Adam step
     out = ref(x0, plain)                               # refined frames [T_out][H][W]
@@ -18,10 +18,11 @@ FEAT_C = 16
 
 
 def features(rec, stream, H: int, W: int, T: int, plain, threshold: float = 1.0):
-    """Refiner input of every frame of `stream` (uses rec's frame stride)."""
+    """Refiner input of every frame of `stream` (uses rec's frame stride): bf16, 16 channels
+    as two channel-chunk planes, [T_out][H][2][W][8]."""
     torch = rec.torch
     T_out = plain.shape[0]
-    x0 = torch.empty((T_out, H, W, FEAT_C), dtype=torch.bfloat16, device=plain.device)
+    x0 = torch.empty((T_out, H, FEAT_C // 8, W, 8), dtype=torch.bfloat16, device=plain.device)
     spk.spk_features(rec.ctx, stream, H, W, T, threshold, plain, x0)
     return x0
 
@@ -80,7 +81,7 @@ class Refiner:
 
 def fit(ref: Refiner, clips, steps: int, lr: float = 1e-3, batch: int = 8, seed: int = 0,
         lr_final: float | None = None):
-    """Train on clips [(x0, plain, gt)] of device tensors ([N][H][W][16], [N][H][W], [N][H][W]).
+    """Train on clips [(x0, plain, gt)] of device tensors ([N][H][2][W][8], [N][H][W], [N][H][W]).
 
     Each step takes `batch` consecutive frames of one clip (a contiguous view, no copy),
     clip and offset drawn from PCG64(seed); the learning rate decays linearly to lr_final

@@ -24,6 +24,12 @@ def _built():
     spk.load()
 
 
+def planar(x):
+    """[N][H][W][16] -> the library's channel-chunk planes [N][H][2][W][8]."""
+    N, H, W, C = x.shape
+    return np.ascontiguousarray(x.reshape(N, H, W, C // 8, 8).transpose(0, 1, 3, 2, 4))
+
+
 def _bf16_bits(a):
     return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).view(torch.int16).numpy()
 
@@ -57,7 +63,7 @@ def test_features_exact(H, W, T, stride, theta):
     torch.cuda.synchronize()
     want = _cpu_features(stream, H, W, T, stride, plain.cpu().numpy(), theta)
     got = x0.view(torch.int16).cpu().numpy()
-    assert np.array_equal(got, _bf16_bits(want))
+    assert np.array_equal(got, _bf16_bits(planar(want)))
 
 
 def _rand_case(N, H, W, seed):
@@ -85,7 +91,7 @@ def test_forward_matches_reference(N, H, W):
     p[-16:] = 0.01
     ref.set_params(p)
     x0, plain, gt = _rand_case(N, H, W, seed=N * 1000 + W)
-    out = ref(_dev(x0, torch.bfloat16), _dev(plain))
+    out = ref(_dev(planar(x0), torch.bfloat16), _dev(plain))
     torch.cuda.synchronize()
     want, _, _ = refnet.forward(p, x0, plain)
     got = out.cpu().numpy()
@@ -103,7 +109,7 @@ def test_gradients_and_loss_match_reference():
     p[refnet.NPARAM - (9 * 32 * 16 + 16):] *= 10
     ref.set_params(p)
     x0, plain, gt = _rand_case(N, H, W, seed=7)
-    loss = ref.train_step(_dev(x0, torch.bfloat16), _dev(plain), _dev(gt), lr=0.0)
+    loss = ref.train_step(_dev(planar(x0), torch.bfloat16), _dev(plain), _dev(gt), lr=0.0)
     g = ref.grads()
     out_ref, loss_ref, g_ref = refnet.forward(p, x0, plain, gt)
     assert math.isclose(loss, loss_ref, rel_tol=1e-3)
@@ -125,7 +131,7 @@ def test_adam_first_step_moves_by_lr_times_sign():
     ref = refiner.Refiner(seed=3)
     p0 = ref.params()
     x0, plain, gt = _rand_case(N, H, W, seed=1)
-    args = (_dev(x0, torch.bfloat16), _dev(plain), _dev(gt))
+    args = (_dev(planar(x0), torch.bfloat16), _dev(plain), _dev(gt))
     ref.train_step(*args, lr=0.0)
     g = ref.grads()
     ref.set_params(p0)                                        # also resets the Adam state
@@ -146,8 +152,8 @@ def test_params_roundtrip_and_checkpoint(tmp_path):
     b.load(str(tmp_path / "w.npy"))
     assert np.array_equal(a.params(), b.params())
     x0, plain, _ = _rand_case(1, 8, 40, seed=2)
-    oa = a(_dev(x0, torch.bfloat16), _dev(plain))
-    ob = b(_dev(x0, torch.bfloat16), _dev(plain))
+    oa = a(_dev(planar(x0), torch.bfloat16), _dev(plain))
+    ob = b(_dev(planar(x0), torch.bfloat16), _dev(plain))
     assert torch.equal(oa, ob)
     with pytest.raises(spk.SpkError):
         spk.spk_refiner_set_params(a.r, np.zeros(5, dtype=np.float32))
@@ -160,10 +166,10 @@ def test_argument_errors():
     x0, plain, _ = _rand_case(1, 4, 8, seed=0)
     host = np.zeros((1, 4, 8), dtype=np.float32)
     with pytest.raises(spk.SpkError) as e:
-        spk.spk_refiner_forward(r.r, None, _dev(x0, torch.bfloat16), host, 1, 4, 8, _dev(plain))
+        spk.spk_refiner_forward(r.r, None, _dev(planar(x0), torch.bfloat16), host, 1, 4, 8, _dev(plain))
     assert e.value.code == spk.SPK_ERR_ARG
     with pytest.raises(spk.SpkError):
-        spk.spk_refiner_forward(r.r, None, _dev(x0, torch.bfloat16), _dev(plain), 0, 4, 8, _dev(plain))
+        spk.spk_refiner_forward(r.r, None, _dev(planar(x0), torch.bfloat16), _dev(plain), 0, 4, 8, _dev(plain))
     r.close()
 
 
