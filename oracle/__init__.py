@@ -1,7 +1,7 @@
 """ORACLE -- test infrastructure only.
 
-A plain fp64 CPU restatement of the paper's FSR and SSR reconstructions (Sec. III-B,
-Def. 2, Eq. 4), written in C (``oracle.c``) and driven through ctypes, plus a pure-Python
+A plain fp64 CPU restatement of the paper's FSR and SSR reconstructions and of the general
+n-order tree (Sec. III-B, Def. 2, Fig. 1, Eq. 4), written in C (``oracle.c``) and driven through ctypes, plus a pure-Python
 literal reading of Def. 2 for tiny inputs (``bruteforce.py``).  Only ``tests/``,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import it; the
 library in ``paper_2412_11639_gb300`` never does, and the two share no code.
@@ -42,6 +42,9 @@ def _load():
         lib.oracle_reconstruct.restype = c.c_int
         lib.oracle_spike_times.argtypes = [c.c_void_p, c.c_int64, c.c_int, c.c_int64, c.c_void_p]
         lib.oracle_spike_times.restype = c.c_int
+        lib.oracle_segments_n.argtypes = [c.c_void_p, c.c_int, c.c_int, c.c_double, c.c_void_p,
+                                          c.c_void_p, c.c_void_p, c.c_void_p]
+        lib.oracle_segments_n.restype = c.c_int
         lib.oracle_tfi.argtypes = [c.c_void_p, c.c_int64, c.c_int64, c.c_int, c.c_double, c.c_int,
                                    c.c_void_p, c.c_int64, c.c_void_p]
         lib.oracle_tfi.restype = c.c_int
@@ -62,6 +65,19 @@ def spike_times(stream: np.ndarray, T: int, p: int) -> np.ndarray:
     out = np.empty(T, dtype=np.int32)
     K = _load().oracle_spike_times(stream.ctypes.data, stream.shape[1], T, p, out.ctypes.data)
     return out[:K].copy()
+
+
+def segments_n(times, n: int, theta: float = 1.0):
+    """Stable sequences of one pixel's spike times under the general n-order tree:
+    [(t_start, t_end, N, value)] (orders 1 and 2 are FSR and SSR)."""
+    s = np.ascontiguousarray(times, dtype=np.int32)
+    K = s.shape[0]
+    cap = max(K, 1)
+    ts, te, nn = (np.empty(cap, dtype=np.int32) for _ in range(3))
+    vv = np.empty(cap, dtype=np.float64)
+    ns = _load().oracle_segments_n(s.ctypes.data, K, n, theta, ts.ctypes.data, te.ctypes.data,
+                                   nn.ctypes.data, vv.ctypes.data)
+    return [(int(ts[j]), int(te[j]), int(nn[j]), float(vv[j])) for j in range(ns)]
 
 
 class Result:
@@ -87,7 +103,8 @@ class Result:
 def reconstruct(stream: np.ndarray, H: int, W: int, T: int, theta: float = 1.0, order: int = 1,
                 stride: int = 1, pixels=None, frames: bool = True,
                 segments: bool = False) -> Result:
-    """Run the oracle on packed stream [T][pitch] for the given pixels (default: all)."""
+    """Run the oracle on packed stream [T][pitch] for the given pixels (default: all).
+    order 1 = FSR, 2 = SSR, n > 2 = the general n-order tree (up to 32)."""
     stream = np.ascontiguousarray(stream, dtype=np.uint8)
     if stream.ndim != 2 or stream.shape[0] < T:
         raise ValueError("stream must be [T][pitch]")

@@ -118,3 +118,39 @@ def tfp_frames(bits, window: int, stride: int = 1, theta=1):
     T = len(bits)
     return [Fraction(theta) * sum(bits[u] for u in range(max(0, k * stride - window + 1), k * stride + 1))
             / window for k in range((T + stride - 1) // stride)]
+
+
+def _ends_n(seq, depth: int, n: int):
+    """Cut positions ('a cut after element i') of a level-`depth` stream under the n-order
+    tree: its own greedy stable sequences, and, below level n, the cuts its two sub-streams
+    ('-' = the smaller value, '+' = the larger, inside each of its stable sequences) send up,
+    each placed after the element at which the breaking sub-stream element ends."""
+    ends = set()
+    for (i0, i1) in greedy_stable_sequences(seq):
+        ends.add(i1)
+        if depth < n:
+            part = seq[i0:i1 + 1]
+            a = min(part)
+            for v in (a, a + 1):
+                pos, d = interval_stream(part, v)
+                if len(d) < 2:
+                    continue
+                for e in _ends_n(d, depth + 1, n):
+                    if e < len(d) - 1:
+                        ends.add(i0 + pos[e + 1])
+    return ends
+
+
+def segments_n(bits, n: int, theta=1):
+    """segments() under the general n-order tree (Fig. 1 caption, Sec. III-B)."""
+    s = spike_times(bits)
+    if len(s) < 2:
+        return []
+    x = [s[i + 1] - s[i] for i in range(len(s) - 1)]
+    out, i0 = [], 0
+    for i in sorted(_ends_n(x, 1, n)):
+        N = i - i0 + 1
+        ts, te = s[i0], s[i + 1]
+        out.append((ts, te, N, Fraction(theta) * N / (te - ts)))
+        i0 = i + 1
+    return out

@@ -17,6 +17,7 @@
  *      to S_1, Fig. 1).  Break each S_2 greedily by the same zero-order rule; a break
  *      before distance d_j = q_{j+1} - q_j cuts S_1 after element q_j.  The cuts of
  *      both choices are united and split the FSR sequence (Sec. III-B);
+ *   (order n > 2: the general n-order tree, oracle_segments_n);
  *   5. intensity of a stable sequence of N intervals: theta / ((1/N) sum T_0(i)) (Eq. 4,
  *      with 255 generalised to the threshold argument theta);
  *   6. frames: frame k samples t_k = k * stride and takes the value of the sequence
@@ -132,6 +133,84 @@ int oracle_segments(const int32_t *s, int K, int order, double theta, int32_t *t
     return nseg;
 }
 
+/*
+ * General n-order stability (Sec. III-B and the caption of Fig. 1): the interval streams
+ * S_1, S_2^1, S_2^2, S_3^1, ... are each broken greedily by the zero-order rule of Def. 2.
+ * Inside every stable sequence of a level-k stream, whose values are {a, a+1}, the two
+ * level-(k+1) streams are the index distances between consecutive occurrences of a (the
+ * '-' choice) and of a+1 (the '+' choice).  A level-(k+1) stable sequence that ends at its
+ * distance j (not the stream's last) cuts the level-k stream after the element at which
+ * distance j ends, so that every cut lands, level by level, on S_1.  The tree stops at
+ * level n, or where a stream has fewer than two elements (the empty S_n^m of Fig. 1).
+ * Orders 1 and 2 are FSR and SSR.
+ *
+ * cut[i] = 1 marks a cut after element i of v[0 .. L-1]; the caller clears cut.
+ */
+static void norder_cuts(const int32_t *v, int L, int depth, int n, int32_t *cut) {
+    int i0 = 0;
+    while (i0 < L) {
+        int lo = v[i0], hi = v[i0], i1 = i0;          /* greedy stable sequence [i0, i1] */
+        while (i1 + 1 < L) {
+            int nlo = v[i1 + 1] < lo ? v[i1 + 1] : lo;
+            int nhi = v[i1 + 1] > hi ? v[i1 + 1] : hi;
+            if (!zero_order_ok(nlo, nhi)) break;
+            lo = nlo;
+            hi = nhi;
+            ++i1;
+        }
+        if (i1 < L - 1) cut[i1] = 1;
+        if (depth < n) {
+            for (int val = lo; val <= lo + 1; ++val) {  /* '-' then '+' */
+                int m = 0;
+                for (int i = i0; i <= i1; ++i)
+                    if (v[i] == val) ++m;
+                if (m < 3) continue;                  /* fewer than two distances: nothing to break */
+                int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+                int32_t *d = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m - 1));
+                int32_t *sub = (int32_t *)calloc((size_t)(m - 1), sizeof(int32_t));
+                m = 0;
+                for (int i = i0; i <= i1; ++i)
+                    if (v[i] == val) pos[m++] = i;
+                for (int j = 0; j + 1 < m; ++j) d[j] = pos[j + 1] - pos[j];
+                norder_cuts(d, m - 1, depth + 1, n, sub);
+                for (int j = 0; j + 2 < m; ++j)
+                    if (sub[j]) cut[pos[j + 1]] = 1;  /* distance j ends at element pos[j+1] */
+                free(pos);
+                free(d);
+                free(sub);
+            }
+        }
+        i0 = i1 + 1;
+    }
+}
+
+/* Steps 2-5 with the n-order tree in place of steps 3-4 (same outputs as oracle_segments). */
+int oracle_segments_n(const int32_t *s, int K, int n, double theta, int32_t *t_start, int32_t *t_end,
+                      int32_t *n_int, double *val) {
+    if (K < 2 || n < 1) return 0;
+    int L = K - 1;
+    int32_t *x = (int32_t *)malloc(sizeof(int32_t) * (size_t)L);
+    int32_t *cut = (int32_t *)calloc((size_t)L, sizeof(int32_t));
+    for (int i = 0; i < L; ++i) x[i] = s[i + 1] - s[i];
+    norder_cuts(x, L, 1, n, cut);
+    cut[L - 1] = 1;                                  /* the last sequence ends at the last spike */
+    int nseg = 0, i0 = 0;
+    for (int i = 0; i < L; ++i) {
+        if (!cut[i]) continue;
+        int N = i - i0 + 1;
+        int ts = s[i0], te = s[i + 1];
+        t_start[nseg] = ts;
+        t_end[nseg] = te;
+        n_int[nseg] = N;
+        val[nseg] = theta / ((double)(te - ts) / (double)N);   /* Eq. 4 */
+        ++nseg;
+        i0 = i + 1;
+    }
+    free(x);
+    free(cut);
+    return nseg;
+}
+
 /* Step 6 for one pixel: frames[k * fstride] for k = 0 .. ceil(T/stride)-1. */
 void oracle_frames(int K, int nseg, const int32_t *t_start, const int32_t *t_end,
                    const double *val, int T, int stride, double *frames, int64_t fstride) {
@@ -169,7 +248,7 @@ int oracle_reconstruct(const uint8_t *stream, int64_t pitch, int64_t P, int T, d
                        int order, int stride, const int64_t *pix, int64_t npix, double *frames,
                        int32_t *K_out, int32_t *nseg_out, const int64_t *seg_off,
                        int32_t *seg_ts, int32_t *seg_te, int32_t *seg_n, double *seg_val) {
-    if (P <= 0 || T <= 0 || pitch * 8 < P || stride <= 0 || order < 1 || order > 2) return -1;
+    if (P <= 0 || T <= 0 || pitch * 8 < P || stride <= 0 || order < 1 || order > 32) return -1;
     if (pix == NULL) npix = P;
     int err = 0;
 #pragma omp parallel
@@ -189,7 +268,8 @@ int oracle_reconstruct(const uint8_t *stream, int64_t pitch, int64_t P, int T, d
                 continue;
             }
             int K = oracle_spike_times(stream, pitch, T, p, s);
-            int ns = oracle_segments(s, K, order, theta, ts, te, nn, vv, work);
+            int ns = order <= 2 ? oracle_segments(s, K, order, theta, ts, te, nn, vv, work)
+                                : oracle_segments_n(s, K, order, theta, ts, te, nn, vv);
             if (K_out) K_out[i] = K;
             if (nseg_out) nseg_out[i] = ns;
             if (seg_off && seg_ts) {

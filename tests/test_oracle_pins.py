@@ -376,3 +376,102 @@ def test_tfi_is_fsr_of_single_intervals_and_tfp_tracks_rate():
         g = oracle.tfp(st, 1, 64, 600, L, 1.0, 1)[L:]
         cnt = np.rint(g * L)
         assert np.all((cnt >= np.floor(L * Q)) & (cnt <= np.ceil(L * Q)))
+
+
+# ------------------------------------------------ general n-order tree (Fig. 1, Sec. III-B) ----
+def _times(b, p):
+    return np.flatnonzero(b[:, p]).astype(np.int32)
+
+
+def _trip(segs):
+    return [tuple(e[:3]) for e in segs]
+
+
+def test_norder_general_code_is_fsr_and_ssr_at_orders_1_and_2():
+    """The tree's code at n = 1 and 2 gives the FSR and SSR sequences of the specialised
+    (separately pinned) oracle, and the literal tree gives the literal FSR and SSR."""
+    rng = np.random.default_rng(3)
+    for seed in range(60):
+        T = int(rng.integers(20, 300))
+        b = spkgen.random_bits(T, 8, rng.uniform(0.1, 0.9), 500 + seed)
+        st = spkgen.pack(b)
+        for n in (1, 2):
+            r = oracle.reconstruct(st, 1, 8, T, 1.0, n, 1, frames=False, segments=True)
+            for p in range(8):
+                ts, te, nn, v = r.segments(p)
+                got = oracle.segments_n(_times(b, p), n)
+                assert _trip(got) == list(zip(ts.tolist(), te.tolist(), nn.tolist()))
+                assert np.array_equal([g[3] for g in got], v)
+                assert _trip(bf.segments_n(b[:, p].tolist(), n)) == _trip(bf.segments(b[:, p].tolist(), n))
+
+
+def _third_order_streams(count, seed):
+    """Streams whose S_2 has several stable sequences of its own: intervals 2 and 3 in
+    patterns with changing spacings, so that the third level has something to cut."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        x = []
+        while sum(x) < 400:
+            gap = int(rng.integers(1, 5))          # occurrences of 3 spaced by 1..4 intervals of 2
+            x += [2] * gap + [3]
+            if rng.uniform() < 0.05:
+                x.append(int(rng.integers(1, 7)))   # occasional FSR break
+        s = np.concatenate([[int(rng.integers(0, 3))], np.cumsum(x) + 2])
+        out.append(s[s < 420].astype(np.int32))
+    return out
+
+
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_norder_matches_literal_tree(n):
+    """C tree == set-based literal tree: on all 2^14 patterns of 14 steps, random streams,
+    and streams built so that levels 3 and up do cut."""
+    T = 14
+    P = 1 << T
+    bits = ((np.arange(P)[None, :] >> np.arange(T)[:, None]) & 1).astype(np.uint8)
+    r = oracle.reconstruct(spkgen.pack(bits), 1, P, T, 1.0, n, 1, frames=False, segments=True)
+    for p in range(0, P, 3):
+        ts, te, nn, _ = r.segments(p)
+        assert list(zip(ts.tolist(), te.tolist(), nn.tolist())) == _trip(bf.segments_n(bits[:, p].tolist(), n))
+    differ = 0
+    for s in _third_order_streams(40, 11 + n):
+        T = int(s[-1]) + 1
+        bits1 = np.zeros(T, dtype=np.uint8)
+        bits1[s] = 1
+        want = bf.segments_n(bits1.tolist(), n)
+        got = oracle.segments_n(s, n)
+        assert _trip(got) == _trip(want)
+        assert np.allclose([g[3] for g in got], [float(w[3]) for w in want], rtol=1e-15, atol=0)
+        differ += _trip(got) != _trip(oracle.segments_n(s, 2))
+    assert differ >= 10            # the third level does cut these streams
+
+
+def test_norder_constant_intensity_is_one_sequence():
+    """Theorem 1 through the tree: by Lemma 2 every S_k of a constant intensity is the
+    interval stream of an integrate-and-fire G_{k-1} with a constant rate, hence stable,
+    so no level cuts: one sequence for every order."""
+    rng = np.random.default_rng(9)
+    Q = rng.uniform(0.03, 1.0, 128)
+    T = 3000
+    st = _const_stream(Q, rng.uniform(0, 1, 128) * Q, T)
+    for n in (3, 4, 6):
+        r = oracle.reconstruct(st, 1, 128, T, 1.0, n, 1, frames=False)
+        assert np.all(r.nseg[r.K >= 2] == 1), n
+
+
+def test_norder_refines_and_saturates():
+    """Each level can only add cuts (the sequences of order n+1 refine those of order n), and
+    past the depth at which every stream is empty nothing changes."""
+    b = spkgen.random_bits(300, 256, 0.45, 77)
+    st = spkgen.pack(b)
+    prev = None
+    for n in range(1, 9):
+        r = oracle.reconstruct(st, 1, 256, 300, 1.0, n, 1, frames=False, segments=True)
+        if prev is not None:
+            for p in range(0, 256, 7):
+                ends = set(r.segments(p)[1].tolist())
+                assert set(prev.segments(p)[1].tolist()) <= ends
+        prev = r
+    r12 = oracle.reconstruct(st, 1, 256, 300, 1.0, 12, 1, frames=False)
+    r32 = oracle.reconstruct(st, 1, 256, 300, 1.0, 32, 1, frames=False)
+    assert np.array_equal(r12.nseg, r32.nseg)
