@@ -42,9 +42,11 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dynamic_250x400x20000")
-    ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3, 4],
-                    help="method: 1 FSR, 2 SSR (default), 3 TFI, 4 TFP (window --tfp-window)")
+    ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3, 4, 5],
+                    help="method: 1 FSR, 2 SSR (default), 3 TFI, 4 TFP (window --tfp-window), "
+                         "5 the n-order tree (--stability-order levels)")
     ap.add_argument("--tfp-window", type=int, default=32)
+    ap.add_argument("--stability-order", type=int, default=3, choices=[3, 4, 5])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["single", "batch", "serve", "refine"], default="single",
@@ -201,7 +203,7 @@ def recorded_traffic(workload: str, order: int):
 
 
 # ------------------------------------------------------------------ CPU oracle ----
-def oracle_rate(st, w, order, pixels=None, window=32):
+def oracle_rate(st, w, order, pixels=None, window=32, n=3):
     """Gpixel-frames/s of the fp64 CPU oracle over the given pixels (all by default)."""
     import oracle
     t0 = time.perf_counter()
@@ -210,7 +212,8 @@ def oracle_rate(st, w, order, pixels=None, window=32):
     elif order == 4:
         r = oracle.tfp(st, w.H, w.W, w.T, window, 1.0, w.stride, pixels=pixels)
     else:
-        r = oracle.reconstruct(st, w.H, w.W, w.T, 1.0, order, w.stride, pixels=pixels, frames=True)
+        r = oracle.reconstruct(st, w.H, w.W, w.T, 1.0, n if order == 5 else order, w.stride, pixels=pixels,
+                               frames=True)
     dt = time.perf_counter() - t0
     npix = w.P if pixels is None else len(pixels)
     del r
@@ -234,13 +237,13 @@ def run_reference(args, rank, world):
     starts = np.arange(0, w.P, chunk)
     for i in range(args.warmup):
         s0 = starts[i % len(starts)]
-        oracle_rate(st, w, args.order, np.arange(s0, min(s0 + chunk, w.P)))
+        oracle_rate(st, w, args.order, np.arange(s0, min(s0 + chunk, w.P)), args.tfp_window, args.stability_order)
     t0 = time.perf_counter()
     units = 0
     for i in range(args.steps):
         s0 = starts[i % len(starts)]
         pix = np.arange(s0, min(s0 + chunk, w.P))
-        oracle_rate(st, w, args.order, pix)
+        oracle_rate(st, w, args.order, pix, args.tfp_window, args.stability_order)
         units += len(pix) * w.T_out
     dt = time.perf_counter() - t0
     value = units / dt / 1e9
@@ -250,7 +253,7 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": config_of(w, args.order),
+        "config": config_of(w, args.order, args.tfp_window, args.stability_order),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{chunk} pixels x {w.T_out} frames per step, rotating over the "
                                    f"{w.P} pixels of {w.name}"},
@@ -260,11 +263,11 @@ def run_reference(args, rank, world):
     return 0
 
 
-METHODS = {1: "FSR", 2: "SSR", 3: "TFI", 4: "TFP"}
+METHODS = {1: "FSR", 2: "SSR", 3: "TFI", 4: "TFP", 5: "n-order"}
 
 
-def config_of(w, order, window=32):
-    name = METHODS[order] + (f"-{window}" if order == 4 else "")
+def config_of(w, order, window=32, n=3):
+    name = METHODS[order] + (f"-{window}" if order == 4 else "") + (f" n={n}" if order == 5 else "")
     return {"workload": w.name, "H": w.H, "W": w.W, "T": w.T, "frame_stride": w.stride,
             "T_out": w.T_out, "out_dtype": w.out_dtype, "method": name,
             "threshold": 1.0, "parallelism": "replicas, one per GPU",
@@ -283,7 +286,7 @@ def run_ours(args, rank, world, local_rank):
     dtype = torch.float16 if w.out_dtype == "f16" else torch.float32
     esz = 2 if dtype == torch.float16 else 4
     R = pkg.Reconstructor(order=args.order, stride=w.stride, dtype=dtype, device=local_rank,
-                          tfp_window=args.tfp_window)
+                          tfp_window=args.tfp_window, stability_order=args.stability_order)
     dev = torch.from_numpy(st).cuda()
     out = R.alloc_frames(w.H, w.W, w.T)
     stream = R.stream
@@ -353,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
         return 0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt, npix = oracle_rate(st, w, args.order, window=args.tfp_window)
+        v, dt, npix = oracle_rate(st, w, args.order, window=args.tfp_window, n=args.stability_order)
         cpu = {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"the whole workload once ({npix} pixels x {w.T_out} frames, {dt:.1f} s)"}
     traffic = recorded_traffic(w.name, args.order)
@@ -361,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic",
-        "config": config_of(w, args.order, args.tfp_window),
+        "config": config_of(w, args.order, args.tfp_window, args.stability_order),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",

@@ -57,17 +57,24 @@ enum spk_dtype { SPK_F32 = 0, SPK_F16 = 1 };
  *  SPK_TFI: theta / the interval (s_i, s_{i+1}] covering t_k (every interval is its own
  *           span, with the frame policy above);
  *  SPK_TFP: theta * (spikes in the tfp_window steps (t_k - L, t_k]) / L, steps before the
- *           stream counting as empty; whole streams only (no spk_stream, no spk_segments). */
-enum spk_method { SPK_FSR = 1, SPK_SSR = 2, SPK_TFI = 3, SPK_TFP = 4 };
+ *           stream counting as empty; whole streams only (no spk_stream, no spk_segments).
+ *  SPK_NORDER: the general n-order stability tree of Sec. III-B (Fig. 1 caption) with
+ *           n = stability_order levels (3..5; orders 1 and 2 are FSR and SSR): inside every
+ *           stable sequence of a level-k stream the '-' and '+' streams of its two values
+ *           (index distances between their occurrences) are segmented by the same rule,
+ *           and each of their breaks cuts the level above after the element where the
+ *           breaking distance ends.  Whole streams only (no spk_stream / spk_run). */
+enum spk_method { SPK_FSR = 1, SPK_SSR = 2, SPK_TFI = 3, SPK_TFP = 4, SPK_NORDER = 5 };
 
 typedef struct spk_config {
-    int method;         /* SPK_FSR, SPK_SSR, SPK_TFI or SPK_TFP */
+    int method;         /* SPK_FSR, SPK_SSR, SPK_TFI, SPK_TFP or SPK_NORDER */
     int frame_stride;   /* >= 1: frame k samples step k * frame_stride */
     int out_dtype;      /* SPK_F32 or SPK_F16 (fp16 is the round-to-nearest-even of the
                            fp32 value) */
     int device;         /* CUDA device ordinal */
     void *stream;       /* cudaStream_t to launch on; NULL = the legacy default stream */
     int tfp_window;     /* SPK_TFP only: window L in steps, 1..64 (the paper uses 32, 64) */
+    int stability_order; /* SPK_NORDER only: levels n of the stability tree, 3..5 */
 } spk_config;
 
 typedef struct spk_ctx spk_ctx;
@@ -275,7 +282,8 @@ int spk_selftest_wait(spk_ctx *ctx, int64_t limit_cycles);
  * device it is loaded on, until the process exits.  It calls no cudaMalloc, cudaFree or
  * allocating library routine.
  *
- *   cfg           method, frame_stride, out_dtype, device, stream, tfp_window, as for
+ *   cfg           method, frame_stride, out_dtype, device, stream, tfp_window,
+ *                 stability_order, as for
  *                 spk_create
  *                 (the stream must belong to cfg->device)
  *   host_stream   host, uint8 [T][spk_pitch(H, W)]

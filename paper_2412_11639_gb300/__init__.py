@@ -23,13 +23,14 @@ __all__ = ["spk", "build", "Reconstructor", "SpkError", "SPK_F32", "SPK_F16", "s
 class Reconstructor:
     """One libspk context bound to a torch CUDA stream.
 
-    order (the method): 1 = FSR, 2 = SSR, 3 = TFI, 4 = TFP (window tfp_window steps);
+    order (the method): 1 = FSR, 2 = SSR, 3 = TFI, 4 = TFP (window tfp_window steps),
+    5 = the general n-order stability tree with stability_order levels (3..5);
     frame k samples step k * stride; dtype torch.float32 or torch.float16.  Device memory
     comes from torch; the reconstruction runs in libspk.
     """
 
     def __init__(self, order: int = 2, stride: int = 1, dtype=None, device: int = 0,
-                 stream=None, tfp_window: int = 32):
+                 stream=None, tfp_window: int = 32, stability_order: int = 3):
         import torch
         self.torch = torch
         dtype = dtype or torch.float32
@@ -39,7 +40,7 @@ class Reconstructor:
         self.order, self.stride, self.device = order, stride, device
         self.stream = stream or torch.cuda.current_stream(device)
         self.ctx = spk_create(order, stride, SPK_F16 if dtype == torch.float16 else SPK_F32,
-                              device, self.stream.cuda_stream, tfp_window)
+                              device, self.stream.cuda_stream, tfp_window, stability_order)
 
     def close(self):
         if self.ctx is not None:

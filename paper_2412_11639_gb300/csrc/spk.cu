@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include <climits>
+#include <type_traits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -82,6 +83,7 @@ struct Job {
     int div_s;
     float theta;    // threshold of Eq. 4
     int window;     // TFP window in steps
+    int order_n;    // levels of the n-order tree (method SPK_NORDER)
     int flags;      // JOB_FIRST | JOB_LAST
     int block0;     // first block of this job in the flat grid
 };
@@ -478,8 +480,11 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     // ------------------------------------------------------------- compute warps ----
     const int64_t p = static_cast<int64_t>(blk) * BLOCK_PIX + warp * 32 + lane;
     const bool valid = p < job.P;
-    spk::PixelScan<ORDER> sc;
-    sc.init();
+    // ORDER 5 is the general n-order tree (job.order_n levels); 1 FSR, 2 SSR, 3 TFI
+    using Scan = std::conditional_t<ORDER == 5, spk::TreeScan, spk::PixelScan<ORDER == 5 ? 1 : ORDER>>;
+    Scan sc;
+    if constexpr (ORDER == 5) sc.init(job.order_n);
+    else sc.init();
 
     FrameSink<OutT> fs;
     SegSink ss;
@@ -499,7 +504,8 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         fs.ct = fs.cur_ke = 0;
         fs.ci = -1;
         fs.cv = fs.cur_v = 0.f;
-        if (!(job.flags & JOB_FIRST) && valid) carry_load(job.carry, job.P, p, sc, fs);
+        if constexpr (ORDER != 5)
+            if (!(job.flags & JOB_FIRST) && valid) carry_load(job.carry, job.P, p, sc, fs);
     }
 
     bool ok = true;
@@ -535,17 +541,27 @@ __global__ void __launch_bounds__(NTHREADS, 3)
                 if constexpr (SEGMENTS) sc.spike(base + b, ss);
                 else sc.spike(base + b, fs);
             }
+            if constexpr (ORDER == 5) {  // the tree's final cuts go to the sink in order
+                if constexpr (SEGMENTS) sc.release(ss);
+                else sc.release(fs);
+            }
             if constexpr (!SEGMENTS) flush_rows(fs, sc.frontier(), valid, false);
         }
     }
     if (!ok) return;
 
+    if constexpr (ORDER == 5)
+        if (valid && sc.bad) atomicOr(prm.status, DEV_INTERNAL);  // (checked again after finish)
     if constexpr (SEGMENTS) {
         sc.finish(ss);
         ss.done();
         if (valid) prm.counts[p] = ss.cnt;
+        if constexpr (ORDER == 5)
+            if (valid && sc.bad) atomicOr(prm.status, DEV_INTERNAL);
     } else if (job.flags & JOB_LAST) {
         sc.finish(fs);
+        if constexpr (ORDER == 5)
+            if (valid && sc.bad) atomicOr(prm.status, DEV_INTERNAL);
         if (valid) fs.cand(TAIL, 0);  // tail hold (0 without spans)
         flush_rows(fs, INT_MAX, valid, true);
         if (valid && fs.bad) atomicOr(prm.status, DEV_INTERNAL);
@@ -553,10 +569,12 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         // piece end: convert the final cuts and write every resolved frame; the last
         // converted cut starts the open span, the rest are pending candidates
         flush_rows(fs, sc.frontier(), valid, true);
-        if (valid) {
-            const int npend = fs.tail - fs.conv;
-            if (npend > 2 || fs.bad) atomicOr(prm.status, DEV_INTERNAL);
-            carry_store(job.carry, job.P, p, sc, fs, npend > 2 ? 2 : npend, fs.conv);
+        if constexpr (ORDER != 5) {
+            if (valid) {
+                const int npend = fs.tail - fs.conv;
+                if (npend > 2 || fs.bad) atomicOr(prm.status, DEV_INTERNAL);
+                carry_store(job.carry, job.P, p, sc, fs, npend > 2 ? 2 : npend, fs.conv);
+            }
         }
     }
     if constexpr (!SEGMENTS) {
@@ -900,6 +918,13 @@ int launch_tfp(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
     return SPK_OK;
 }
 
+// the n-order tree runs single whole streams only (one job per launch)
+template <typename OutT, bool SEG, int MAXJ>
+int launch_norder(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
+    if constexpr (MAXJ == 1) return launch<5, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
+    else return fail(ctx, SPK_ERR_ARG, "the n-order tree runs whole streams only");
+}
+
 template <int MAXJ, int TT>
 int dispatch_tile(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
     const int m = ctx->cfg.method;
@@ -917,9 +942,12 @@ int dispatch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks, bool segments, i
     const int m = ctx->cfg.method;
     const bool f16 = ctx->cfg.out_dtype == SPK_F16;
     if (segments)
-        return m == SPK_FSR ? launch<1, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
-             : m == SPK_TFI ? launch<3, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
-                            : launch<2, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+        return m == SPK_FSR      ? launch<1, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
+             : m == SPK_TFI      ? launch<3, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
+             : m == SPK_NORDER   ? launch_norder<float, true>(ctx, prm, nblocks)
+                                 : launch<2, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+    if (m == SPK_NORDER)
+        return f16 ? launch_norder<__half, false>(ctx, prm, nblocks) : launch_norder<float, false>(ctx, prm, nblocks);
     if (m == SPK_TFI)
         return f16 ? launch<3, __half, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
                    : launch<3, float, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
@@ -933,11 +961,12 @@ int dispatch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks, bool segments, i
 // the tile a call will use: the context's for FSR / SSR, the default for the others
 int tile_of(const spk_ctx *ctx, bool segments) {
     const int m = ctx->cfg.method;
-    return (segments || m == SPK_TFI || m == SPK_TFP) ? TT_DEFAULT : ctx->tile;
+    return (segments || m == SPK_TFI || m == SPK_TFP || m == SPK_NORDER) ? TT_DEFAULT : ctx->tile;
 }
 
 bool valid_method(const spk_config *cfg) {
-    if (cfg->method < SPK_FSR || cfg->method > SPK_TFP) return false;
+    if (cfg->method < SPK_FSR || cfg->method > SPK_NORDER) return false;
+    if (cfg->method == SPK_NORDER) return cfg->stability_order >= 3 && cfg->stability_order <= spk::TREE_MAX;
     return cfg->method != SPK_TFP || (cfg->tfp_window >= 1 && cfg->tfp_window <= 64);
 }
 
@@ -967,6 +996,7 @@ int fill_job(spk_ctx *ctx, CUtensorMap *map, Job *job, const uint8_t *stream, in
     }
     job->theta = threshold;
     job->window = ctx->cfg.tfp_window;
+    job->order_n = ctx->cfg.stability_order;
     job->flags = flags;
     job->block0 = block0;
     return static_cast<int>((P + BLOCK_PIX - 1) / BLOCK_PIX);
@@ -1011,7 +1041,7 @@ int spk_create(spk_ctx **out, const spk_config *cfg) {
     if (!out) return fail(nullptr, SPK_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!cfg) return fail(nullptr, SPK_ERR_ARG, "cfg is NULL");
-    if (!valid_method(cfg)) return fail(nullptr, SPK_ERR_ARG, "method must be 1..4 (TFP: tfp_window 1..64)");
+    if (!valid_method(cfg)) return fail(nullptr, SPK_ERR_ARG, "method must be 1..5 (TFP: tfp_window 1..64; NORDER: stability_order 3..5)");
     if (cfg->frame_stride < 1) return fail(nullptr, SPK_ERR_ARG, "frame_stride must be >= 1");
     if (cfg->out_dtype != SPK_F32 && cfg->out_dtype != SPK_F16) return fail(nullptr, SPK_ERR_ARG, "bad out_dtype");
     int ndev = 0;
@@ -1108,7 +1138,8 @@ int spk_stream_open(spk_ctx *ctx, int H, int W, int T, spk_stream **out) {
     ctx->msg[0] = 0;
     if (!out) return fail(ctx, SPK_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (ctx->cfg.method == SPK_TFP) return fail(ctx, SPK_ERR_ARG, "TFP runs whole streams only");
+    if (ctx->cfg.method == SPK_TFP || ctx->cfg.method == SPK_NORDER)
+        return fail(ctx, SPK_ERR_ARG, "TFP and the n-order tree run whole streams only");
     if (H <= 0 || W <= 0 || T <= 0 || T > (1 << 30)) return fail(ctx, SPK_ERR_ARG, "bad H, W or T");
     if (static_cast<int64_t>(H) * W > (1LL << 31) - BLOCK_PIX) return fail(ctx, SPK_ERR_ARG, "H*W too large");
     if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
@@ -1181,7 +1212,8 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
         if (!is_device_ptr(jb.stream) || !is_device_ptr(jb.out_frames))
             return fail(ctx, SPK_ERR_ARG, "job %d: stream and out_frames must be device memory", k);
         if (jb.state) {
-            if (ctx->cfg.method == SPK_TFP) return fail(ctx, SPK_ERR_ARG, "TFP runs whole streams only");
+            if (ctx->cfg.method == SPK_TFP || ctx->cfg.method == SPK_NORDER)
+        return fail(ctx, SPK_ERR_ARG, "TFP and the n-order tree run whole streams only");
             if (jb.state->H != jb.H || jb.state->W != jb.W) return fail(ctx, SPK_ERR_ARG, "job %d: H, W differ from its stream", k);
             if (jb.state->pushed + jb.n > jb.state->T) return fail(ctx, SPK_ERR_ARG, "job %d: piece runs past the stream's T", k);
             if (jb.state->device != ctx->cfg.device) return fail(ctx, SPK_ERR_ARG, "job %d: stream on another device", k);
@@ -1389,7 +1421,7 @@ size_t round256(size_t n) { return (n + 255) / 256 * 256; }
 extern "C" int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t *host_stream, int H, int W,
                                             int T, float threshold, void *host_frames) {
     if (!cfg) return fail(nullptr, SPK_ERR_ARG, "cfg is NULL");
-    if (!valid_method(cfg)) return fail(nullptr, SPK_ERR_ARG, "method must be 1..4 (TFP: tfp_window 1..64)");
+    if (!valid_method(cfg)) return fail(nullptr, SPK_ERR_ARG, "method must be 1..5 (TFP: tfp_window 1..64; NORDER: stability_order 3..5)");
     if (cfg->frame_stride < 1) return fail(nullptr, SPK_ERR_ARG, "frame_stride must be >= 1");
     if (cfg->out_dtype != SPK_F32 && cfg->out_dtype != SPK_F16) return fail(nullptr, SPK_ERR_ARG, "bad out_dtype");
     if (cfg->device < 0 || cfg->device >= NOALLOC_MAX_DEVICES) return fail(nullptr, SPK_ERR_ARG, "bad device ordinal");

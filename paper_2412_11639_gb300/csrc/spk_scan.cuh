@@ -161,4 +161,156 @@ struct PixelScan {
     }
 };
 
+// General n-order stability (the tree in the caption of Fig. 1, Sec. III-B), orders 3..5.
+//
+// Every stream of the tree is segmented online by the same greedy zero-order rule as
+// S_1: node 0 is S_1, and the children of node k are the '-' and '+' streams of the
+// values of its open stable sequence (heap order: 2k + 1 for the sequence's first value,
+// 2k + 2 for the other one), whose elements are the index distances between consecutive
+// occurrences of that value inside the sequence.  Every element carries the cut "after
+// this element" expressed on S_1 -- (spike time, S_1 index) of the S_1 element at which
+// it ends -- so that a node whose new element breaks its sequence emits the cut of its
+// previous element, and a break of a node ends (resets) the sequences of all its
+// descendants.  The levels stop at the order n.
+//
+// Cuts of deep nodes lie arbitrarily far in the past, so they wait, sorted and without
+// duplicates, in a per-pixel list until they are final: a node can only emit the cut of
+// its latest element, so every cut at or before the minimum of those over the nodes with
+// an open sequence (frontier()) is final and goes to the sink in order.
+constexpr int TREE_MAX = 5;                       // deepest order
+constexpr int TREE_NODES = (1 << TREE_MAX) - 1;
+constexpr int TREE_PEND = 48;                     // pending cuts per pixel
+
+struct TreeScan {
+    int n;                      // order (number of levels)
+    int last_t, nint;           // S_1 bookkeeping, as in PixelScan
+    int cnt[TREE_NODES];        // elements in the node's open sequence (0: none)
+    int v0[TREE_NODES], v1[TREE_NODES];  // its first value and the other value (0: none yet)
+    int q0[TREE_NODES], q1[TREE_NODES];  // last occurrence (node element index) of v0 / v1, -1: none
+    int jn[TREE_NODES];         // next element index of the node's stream
+    int pct[TREE_NODES], pci[TREE_NODES];  // cut after the node's latest element
+    int pt[TREE_PEND], pi[TREE_PEND], np;  // pending cuts, increasing t
+    int rel_t;                  // last cut handed to the sink
+    int bad;                    // pending list overflowed, or a cut arrived behind the frontier
+
+    SPK_DEV void init(int order) {
+        n = order;
+        last_t = -1;
+        nint = 0;
+        for (int k = 0; k < TREE_NODES; ++k) {
+            cnt[k] = 0;
+            q0[k] = q1[k] = -1;
+            jn[k] = 0;
+        }
+        np = 0;
+        rel_t = -1;
+        bad = 0;
+    }
+    SPK_DEV void first_spike(int t) { last_t = t; }
+    SPK_DEV bool absorb_ones(int) { return false; }
+
+    SPK_DEV int frontier() const {
+        int S = last_t;
+        for (int k = 0; k < (1 << n) - 1; ++k)
+            if (cnt[k] && pct[k] < S) S = pct[k];
+        return S;
+    }
+    SPK_DEV void push(int t, int i) {
+        if (t <= rel_t) {               // handed over already (equal) -- earlier would be a fault
+            if (t < rel_t) bad = 1;
+            return;
+        }
+        int j = np;
+        while (j > 0 && pt[j - 1] > t) --j;
+        if (j > 0 && pt[j - 1] == t) return;  // the same cut from two levels
+        if (np == TREE_PEND) {
+            bad = 1;
+            return;
+        }
+        for (int m = np; m > j; --m) {
+            pt[m] = pt[m - 1];
+            pi[m] = pi[m - 1];
+        }
+        pt[j] = t;
+        pi[j] = i;
+        ++np;
+    }
+    // the sequences of every descendant of node k (at `level`) end
+    SPK_DEV void reset_below(int k, int level) {
+        int lo = 2 * k + 1, hi = 2 * k + 2;  // nodes of the next level under k
+        for (int lev = level + 1; lev <= n; ++lev) {
+            for (int d = lo; d <= hi; ++d) {
+                cnt[d] = 0;
+                q0[d] = q1[d] = -1;
+            }
+            lo = 2 * lo + 1;
+            hi = 2 * hi + 2;
+        }
+    }
+    // element x, whose own cut is (ct, ci), arrives at node k of the given level; then the
+    // distance it closes travels down the branch of its value
+    SPK_DEV void element(int k, int level, int x, int ct, int ci) {
+        for (;;) {
+            const int j = jn[k]++;
+            if (cnt[k] == 0) {
+                v0[k] = x;
+                v1[k] = 0;
+            } else if (x != v0[k] && x != v1[k]) {
+                if (v1[k] == 0 && (x - v0[k] == 1 || v0[k] - x == 1)) {
+                    v1[k] = x;
+                } else {                     // zero-order rule broken: the sequence ends after
+                    push(pct[k], pci[k]);    // the previous element, x opens the next one
+                    v0[k] = x;
+                    v1[k] = 0;
+                    cnt[k] = 0;
+                    q0[k] = q1[k] = -1;
+                    reset_below(k, level);
+                }
+            }
+            ++cnt[k];
+            pct[k] = ct;
+            pci[k] = ci;
+            if (level >= n) return;
+            const int b = x == v0[k] ? 0 : 1;
+            const int prev = b ? q1[k] : q0[k];
+            if (b) q1[k] = j;
+            else q0[k] = j;
+            if (prev < 0) return;
+            x = j - prev;
+            k = 2 * k + 1 + b;
+            ++level;
+        }
+    }
+    template <class Sink>
+    SPK_DEV void spike(int t, Sink &) {
+        element(0, 1, t - last_t, t, nint);
+        ++nint;
+        last_t = t;
+    }
+    // hand every final pending cut to the sink, in time order
+    template <class Sink>
+    SPK_DEV void release(Sink &sink, int S) {
+        int m = 0;
+        while (m < np && pt[m] <= S) {
+            sink.cand(pt[m], pi[m]);
+            rel_t = pt[m];
+            ++m;
+        }
+        if (m) {
+            for (int j = m; j < np; ++j) {
+                pt[j - m] = pt[j];
+                pi[j - m] = pi[j];
+            }
+            np -= m;
+        }
+    }
+    template <class Sink>
+    SPK_DEV void release(Sink &sink) { release(sink, frontier()); }
+    template <class Sink>
+    SPK_DEV void finish(Sink &sink) {
+        if (nint >= 1) push(last_t, nint - 1);
+        release(sink, 0x7fffffff);
+    }
+};
+
 }  // namespace spk

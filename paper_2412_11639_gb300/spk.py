@@ -13,7 +13,7 @@ from .build import LIB
 
 SPK_OK, SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM, SPK_ERR_TIMEOUT, SPK_ERR_INTERNAL = 0, -1, -2, -3, -4, -5
 SPK_F32, SPK_F16 = 0, 1
-SPK_FSR, SPK_SSR, SPK_TFI, SPK_TFP = 1, 2, 3, 4
+SPK_FSR, SPK_SSR, SPK_TFI, SPK_TFP, SPK_NORDER = 1, 2, 3, 4, 5
 
 _c = ctypes
 EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
@@ -35,7 +35,8 @@ class SpkError(RuntimeError):
 
 class spk_config(ctypes.Structure):
     _fields_ = [("method", _c.c_int), ("frame_stride", _c.c_int), ("out_dtype", _c.c_int),
-                ("device", _c.c_int), ("stream", _c.c_void_p), ("tfp_window", _c.c_int)]
+                ("device", _c.c_int), ("stream", _c.c_void_p), ("tfp_window", _c.c_int),
+                ("stability_order", _c.c_int)]
 
 
 class spk_job(ctypes.Structure):
@@ -141,9 +142,9 @@ def _check(ctx, rc):
 
 
 def spk_create(method: int = SPK_SSR, frame_stride: int = 1, out_dtype: int = SPK_F32, device: int = 0,
-               stream: int | None = None, tfp_window: int = 32):
+               stream: int | None = None, tfp_window: int = 32, stability_order: int = 3):
     lib = load()
-    cfg = spk_config(method, frame_stride, out_dtype, device, stream, tfp_window)
+    cfg = spk_config(method, frame_stride, out_dtype, device, stream, tfp_window, stability_order)
     ctx = _c.c_void_p()
     rc = lib.spk_create(_c.byref(ctx), _c.byref(cfg))
     _check(None, rc)
@@ -196,10 +197,11 @@ def spk_selftest_wait(ctx, limit_cycles: int):
 
 def spk_reconstruct_host_noalloc(host_stream, H, W, T, threshold, host_frames, order: int = 2,
                                  frame_stride: int = 1, out_dtype: int = SPK_F32, device: int = 0,
-                                 stream: int | None = None, tfp_window: int = 32):
+                                 stream: int | None = None, tfp_window: int = 32,
+                                 stability_order: int = 3):
     """Host-buffer reconstruction staged in the library's fixed device array (no allocation);
     `order` is the method (1 FSR, 2 SSR, 3 TFI, 4 TFP)."""
-    cfg = spk_config(order, frame_stride, out_dtype, device, stream, tfp_window)
+    cfg = spk_config(order, frame_stride, out_dtype, device, stream, tfp_window, stability_order)
     rc = load().spk_reconstruct_host_noalloc(_c.byref(cfg), _addr(host_stream), H, W, T, threshold,
                                              _addr(host_frames))
     return _check(None, rc)

@@ -47,9 +47,10 @@ def test_layout_helpers(lib):
 def test_create_rejects_bad_config(lib):
     out = ctypes.c_void_p()
     assert lib.spk_create(ctypes.byref(out), None) == spk.SPK_ERR_ARG
-    for cfg in (spk.spk_config(5, 1, 0, 0, None, 32), spk.spk_config(0, 1, 0, 0, None, 32),
-                spk.spk_config(2, 0, 0, 0, None, 32), spk.spk_config(1, 1, 7, 0, None, 32),
-                spk.spk_config(4, 1, 0, 0, None, 0), spk.spk_config(4, 1, 0, 0, None, 65)):
+    for cfg in (spk.spk_config(6, 1, 0, 0, None, 32, 3), spk.spk_config(0, 1, 0, 0, None, 32, 3),
+                spk.spk_config(2, 0, 0, 0, None, 32, 3), spk.spk_config(1, 1, 7, 0, None, 32, 3),
+                spk.spk_config(4, 1, 0, 0, None, 0, 3), spk.spk_config(4, 1, 0, 0, None, 65, 3),
+                spk.spk_config(5, 1, 0, 0, None, 32, 2), spk.spk_config(5, 1, 0, 0, None, 32, 6)):
         assert lib.spk_create(ctypes.byref(out), ctypes.byref(cfg)) == spk.SPK_ERR_ARG
         assert out.value is None
         assert spk.spk_last_error(None)

@@ -1,0 +1,101 @@
+"""The general n-order stability tree (Sec. III-B, Fig. 1 caption) on the GPU against the
+fp64 oracle: sequence boundaries and interval counts bit-exact, fp32 values within 1e-6
+relative, fp16 frames the round-to-nearest-even of the fp32 value."""
+import numpy as np
+import pytest
+
+import oracle
+import spkgen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2412_11639_gb300 as pkg
+    pkg.build()
+    return pkg
+
+
+def _check(pkg, st, H, W, T, n, stride, f16=False):
+    R = pkg.Reconstructor(order=5, stability_order=n, stride=stride,
+                          dtype=torch.float16 if f16 else torch.float32)
+    dev = torch.from_numpy(np.ascontiguousarray(st)).cuda()
+    frames = R(dev, H, W, T).cpu().numpy().reshape(-1, H * W)
+    counts, ts, te, nn, v = [a.cpu().numpy() for a in R.segments(dev, H, W, T)]
+    R.synchronize()                      # raises on a device-side consistency failure
+    R.close()
+    r = oracle.reconstruct(st, H, W, T, 1.0, n, stride, segments=True)
+    assert np.array_equal(counts, r.nseg)
+    for p in range(H * W):
+        k = counts[p]
+        ots, ote, onn, ov = r.segments(p)
+        assert np.array_equal(ts[:k, p], ots) and np.array_equal(te[:k, p], ote), p
+        assert np.array_equal(nn[:k, p], onn), p
+        assert np.all(np.abs(v[:k, p] - ov) <= REL_TOL * np.abs(ov)), p
+    if f16:
+        assert np.array_equal(frames.view(np.uint16), r.frames.astype(np.float32).astype(np.float16).view(np.uint16))
+    else:
+        assert np.all(np.abs(frames - r.frames) <= REL_TOL * np.abs(r.frames))
+    return r
+
+
+def _deep_streams(P, T, seed):
+    """One pixel per constructed stream: intervals 2 with 3s spaced by 1..4 intervals, so
+    that S_2 and S_3 have several stable sequences; occasional FSR breaks."""
+    rng = np.random.default_rng(seed)
+    bits = np.zeros((T, P), dtype=np.uint8)
+    for p in range(P):
+        t = int(rng.integers(0, 4))
+        while t < T:
+            bits[t, p] = 1
+            for _ in range(int(rng.integers(1, 5))):
+                t += 2
+                if t < T:
+                    bits[t, p] = 1
+            t += 3 if rng.uniform() > 0.05 else int(rng.integers(1, 7))
+    return bits
+
+
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_norder_deep_streams(env, n):
+    H, W, T = 3, 97, 1500
+    bits = _deep_streams(H * W, T, 40 + n)
+    r = _check(env, spkgen.pack(bits, H, W), H, W, T, n, 1)
+    r2 = oracle.reconstruct(spkgen.pack(bits, H, W), H, W, T, 1.0, 2, 1, frames=False)
+    assert (r.nseg > r2.nseg).sum() > H * W // 2      # the deeper levels do cut here
+
+
+@pytest.mark.parametrize("n,H,W,T,stride,density,f16", [
+    (3, 1, 7, 5, 1, 0.6, False),
+    (3, 5, 53, 777, 3, 0.4, False),
+    (4, 17, 31, 1000, 1, 0.5, True),
+    (5, 4, 64, 2000, 7, 0.3, False),
+    (3, 2, 200, 3001, 1, 1.0, False),      # a spike every step
+    (4, 2, 200, 300, 1, 0.0, False),       # no spikes
+])
+def test_norder_random_streams(env, n, H, W, T, stride, density, f16):
+    b = spkgen.random_bits(T, H * W, density, seed=n * 100 + W + T)
+    _check(env, spkgen.pack(b, H, W), H, W, T, n, stride, f16)
+
+
+@pytest.mark.parametrize("n", [3, 5])
+def test_norder_scene_workload(env, n):
+    w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=30, W=70, T=4000)
+    st, _ = spkgen.make_stream(w)
+    _check(env, st, w.H, w.W, w.T, n, w.stride)
+
+
+def test_norder_runs_whole_streams_only(env):
+    from paper_2412_11639_gb300 import spk
+    R = env.Reconstructor(order=5, stability_order=3)
+    dev = torch.zeros((100, spkgen.pitch(4, 8)), dtype=torch.uint8, device="cuda")
+    out = R.alloc_frames(4, 8, 100)
+    with pytest.raises(spk.SpkError):
+        env.spk_run(R.ctx, [(dev, 4, 8, 100, 1.0, out, None)])
+    R.close()
