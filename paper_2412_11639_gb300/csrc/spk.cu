@@ -215,8 +215,8 @@ struct FrameSink {
     int bad;         // set if a flush found no record for a frame (never expected)
     int ct, ci;      // the last converted cut (the first spike and -1 before the first)
     float cv;        // value of the last converted span (0 before the first)
-    int cur_ke;      // cursor: the record at head covers frames up to cur_ke, value cur_v
-    float cur_v;
+    int cur_ke;      // cursor: the record at head covers frames up to cur_ke, value cur_o
+    OutT cur_o;
 
     __device__ __forceinline__ int slot(int j) const { return (j & (QCAP - 1)) * 32; }
     __device__ __forceinline__ int frame_of(int t) const {  // t / stride, t >= 0
@@ -225,7 +225,7 @@ struct FrameSink {
     __device__ __forceinline__ void load() {
         const int s = slot(head);
         cur_ke = rt[s];
-        cur_v = __int_as_float(ri[s]);
+        cur_o = to_out<OutT>(__int_as_float(ri[s]));
     }
     // A candidate that arrived one place early is swapped in front of its predecessor
     // (converted records are final and never move).
@@ -275,7 +275,7 @@ struct FrameSink {
         convert(head + 2);  // the ring holds QCAP records, so these two are final
         load();
         const int kl = min(cur_ke, T_out - 1);
-        for (int k = W; k <= kl; ++k) col[static_cast<int64_t>(k) * P] = to_out<OutT>(cur_v);
+        for (int k = W; k <= kl; ++k) col[static_cast<int64_t>(k) * P] = cur_o;
         if (kl + 1 > W) W = kl + 1;
         ++head;
     }
@@ -356,6 +356,7 @@ __device__ __forceinline__ void flush_rows(FrameSink<OutT> &sk, int frontier, bo
     const int klo = valid ? sk.W : INT_MAX;
     if (!valid) lim = 0;
     if (sk.W < lim) sk.load();
+    // one row per iteration for the whole warp, so that the lanes' stores coalesce
     OutT *ptr = sk.col + static_cast<int64_t>(Wmin) * sk.P;
     for (int k = Wmin; k < khi; ++k, ptr += sk.P) {
         if (k >= klo && k < lim) {
@@ -367,7 +368,7 @@ __device__ __forceinline__ void flush_rows(FrameSink<OutT> &sk, int frontier, bo
                 ++sk.head;
                 sk.load();
             }
-            *ptr = to_out<OutT>(sk.cur_v);
+            *ptr = sk.cur_o;
         }
     }
     if (lim > sk.W) sk.W = lim;
@@ -503,7 +504,8 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         fs.head = fs.tail = fs.sorted = fs.conv = fs.W = fs.kf = fs.bad = 0;
         fs.ct = fs.cur_ke = 0;
         fs.ci = -1;
-        fs.cv = fs.cur_v = 0.f;
+        fs.cv = 0.f;
+        fs.cur_o = to_out<OutT>(0.f);
         if constexpr (ORDER != 5)
             if (!(job.flags & JOB_FIRST) && valid) carry_load(job.carry, job.P, p, sc, fs);
     }
@@ -545,7 +547,9 @@ __global__ void __launch_bounds__(NTHREADS, 3)
                 if constexpr (SEGMENTS) sc.release(ss);
                 else sc.release(fs);
             }
-            if constexpr (!SEGMENTS) flush_rows(fs, sc.frontier(), valid, false);
+            // rows go out every second word (64 steps): half the warp reductions of the flush
+            if constexpr (!SEGMENTS)
+                if ((h & 1) || h == WPT - 1) flush_rows(fs, sc.frontier(), valid, false);
         }
     }
     if (!ok) return;
