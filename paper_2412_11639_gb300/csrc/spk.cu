@@ -43,7 +43,8 @@ constexpr int BLOCK_PIX = NCW * 32;      // pixels per block
 constexpr int ROW_BYTES = BLOCK_PIX / 8; // bytes of one frame row per block (TMA box x)
 constexpr int TT_DEFAULT = 64;           // steps per TMA tile (box y); 32, 64 or 128
 constexpr int NS = 4;                    // pipeline stages
-constexpr int QCAP = 32;                 // records per lane
+constexpr int QCAP = 32;        // records per lane
+constexpr int FLUSH_WORDS = 8;  // 32-step words between two row flushes of a warp
 constexpr int NTHREADS = (NCW + 1) * 32; // + one producer warp
 constexpr unsigned FULL = 0xffffffffu;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bounded waits
@@ -547,9 +548,10 @@ __global__ void __launch_bounds__(NTHREADS, 3)
                 if constexpr (SEGMENTS) sc.release(ss);
                 else sc.release(fs);
             }
-            // rows go out every second word (64 steps): half the warp reductions of the flush
+            // rows go out every FLUSH_WORDS words: fewer warp reductions of the flush
             if constexpr (!SEGMENTS)
-                if ((h & 1) || h == WPT - 1) flush_rows(fs, sc.frontier(), valid, false);
+                if (((j * WPT + h) % FLUSH_WORDS) == FLUSH_WORDS - 1 || (j == job.ntiles - 1 && h == WPT - 1))
+                    flush_rows(fs, sc.frontier(), valid, false);
         }
     }
     if (!ok) return;
