@@ -275,34 +275,41 @@ __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CU
     };
 
     if (warp == 4) {  // ------------------------------------------------ TMA producer ----
-        if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
-            int sl = 0, ph = 0, issued = 0;  // ring slot, its phase, loads issued
-            bool ok = true;
-            for (int64_t task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
-                int n, x0, y0, y1;
-                geometry(task, n, x0, y0, y1);
-                for (int r = y0 - 1; r <= y1; ++r) {
-                    // the slot's previous row must have been released (from the second round on)
-                    if (issued >= RING && !mbar_wait(&empty[sl], ph ^ 1, status)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_expect_tx(&full[sl], ROW_TX);
-                    for (int ch = 0; ch < CH; ++ch)
-                        for (int j = 0; j < HALO_PX / TMA_PX; ++j)
-                            tma_load_4d(sbase + sl * L::SLOT + ch * L::PLANE + j * TMA_PX * 16, &xmap, &full[sl],
-                                        (x0 - 1 + j * TMA_PX) * 8, ch, r, n);
-                    ++issued;
-                    if (++sl == RING) sl = 0, ph ^= 1;
+        // lane 0 waits for the slot and arms its barrier; then CH x 5 lanes issue one box each
+        constexpr int BOXES = CH * (HALO_PX / TMA_PX);
+        static_assert(BOXES <= 32, "one box per lane");
+        if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
+        int sl = 0, ph = 0, issued = 0;  // ring slot, its phase, loads issued (the same in every lane)
+        bool ok = true;
+        for (int64_t task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+            int n, x0, y0, y1;
+            geometry(task, n, x0, y0, y1);
+            for (int r = y0 - 1; r <= y1; ++r) {
+                // the slot's previous row must have been released (from the second round on)
+                bool go = true;
+                if (lane == 0) {
+                    if (issued >= RING) go = mbar_wait(&empty[sl], ph ^ 1, status);
+                    if (go) mbar_expect_tx(&full[sl], ROW_TX);
                 }
+                if (!__shfl_sync(0xffffffffu, go, 0)) {
+                    ok = false;
+                    break;
+                }
+                if (lane < BOXES) {
+                    const int ch = lane / (HALO_PX / TMA_PX), j = lane % (HALO_PX / TMA_PX);
+                    tma_load_4d(sbase + sl * L::SLOT + ch * L::PLANE + j * TMA_PX * 16, &xmap, &full[sl],
+                                (x0 - 1 + j * TMA_PX) * 8, ch, r, n);
+                }
+                ++issued;
+                if (++sl == RING) sl = 0, ph ^= 1;
             }
-            // let every issued copy land before this thread leaves: the last min(issued, RING) loads
+        }
+        // let every issued copy land before this warp leaves: the last min(issued, RING) loads
+        if (lane == 0)
             for (int k = 0; k < RING && k < issued; ++k) {
                 if (--sl < 0) sl = RING - 1, ph ^= 1;
                 if (!mbar_wait(&full[sl], ph, status)) break;
             }
-        }
     } else if (warp == 5) {  // ----------------------------------------- MMA issuer ----
         if (lane == 0) {
             // descriptors are linear in the start address (bits 0-13 hold address / 16), so every
