@@ -356,12 +356,22 @@ def run_ours(args, rank, world, local_rank):
         return 0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
+        import numpy as np
+
+        import oracle
         v, dt, npix = oracle_rate(st, w, args.order, window=args.tfp_window, n=args.stability_order)
         cpu = {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                "sample": f"the whole workload once ({npix} pixels x {w.T_out} frames, {dt:.1f} s)"}
+        oracle.set_threads(1)   # the same oracle on one core, on the first 2048 pixels
+        v1, dt1, n1 = oracle_rate(st, w, args.order, np.arange(min(2048, w.P)), args.tfp_window,
+                                  args.stability_order)
+        oracle.set_threads(0)
+        cpu["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} pixels x {w.T_out} frames, {dt1:.1f} s"}
     traffic = recorded_traffic(w.name, args.order)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "input_Gpixel_steps_per_s": w.P * w.T * K * world / (total_ms / 1e3) / 1e9,
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic",
         "config": config_of(w, args.order, args.tfp_window, args.stability_order),

@@ -42,6 +42,8 @@ def _load():
         lib.oracle_reconstruct.restype = c.c_int
         lib.oracle_spike_times.argtypes = [c.c_void_p, c.c_int64, c.c_int, c.c_int64, c.c_void_p]
         lib.oracle_spike_times.restype = c.c_int
+        lib.oracle_set_threads.argtypes = [c.c_int]
+        lib.oracle_set_threads.restype = None
         lib.oracle_segments_n.argtypes = [c.c_void_p, c.c_int, c.c_int, c.c_double, c.c_void_p,
                                           c.c_void_p, c.c_void_p, c.c_void_p]
         lib.oracle_segments_n.restype = c.c_int
@@ -65,6 +67,11 @@ def spike_times(stream: np.ndarray, T: int, p: int) -> np.ndarray:
     out = np.empty(T, dtype=np.int32)
     K = _load().oracle_spike_times(stream.ctypes.data, stream.shape[1], T, p, out.ctypes.data)
     return out[:K].copy()
+
+
+def set_threads(n: int = 0):
+    """Threads of the pixel loops (0: every core)."""
+    _load().oracle_set_threads(n)
 
 
 def segments_n(times, n: int, theta: float = 1.0):

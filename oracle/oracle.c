@@ -33,6 +33,18 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the OpenMP loops over pixels (the CPU-baseline timing runs both 1 and all). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
 
 /* bit of pixel p in frame n of a [T][pitch] LSB-first packed stream */
 static int spike_bit(const uint8_t *stream, int64_t pitch, int n, int64_t p) {

@@ -475,3 +475,27 @@ def test_norder_refines_and_saturates():
     r12 = oracle.reconstruct(st, 1, 256, 300, 1.0, 12, 1, frames=False)
     r32 = oracle.reconstruct(st, 1, 256, 300, 1.0, 32, 1, frames=False)
     assert np.array_equal(r12.nseg, r32.nseg)
+
+
+def test_constant_span_is_tfp_over_that_span():
+    """A pixel with one stable sequence (constant intensity): its value theta N / D is TFP
+    with the window equal to the sequence, read at the sequence's last spike (the N spikes
+    in (t_start, t_end] over D steps) -- the special case of Sec. II."""
+    rng = np.random.default_rng(31)
+    Q = rng.uniform(0.1, 1.0, 64)
+    T = 60
+    st = _const_stream(Q, rng.uniform(0, 1, 64) * Q, T)
+    r = oracle.reconstruct(st, 1, 64, T, 1.0, 2, 1, frames=False, segments=True)
+    checked = 0
+    for p in range(64):
+        if r.nseg[p] != 1:
+            continue
+        ts, te, n, v = (a[0] for a in r.segments(p))
+        D = int(te - ts)
+        if D > 64:
+            continue
+        f = oracle.tfp(st, 1, 64, T, D, 1.0, 1, pixels=[p])
+        assert f[int(te), 0] == pytest.approx(float(v), rel=1e-15)
+        assert v == pytest.approx(n / D, rel=1e-15)
+        checked += 1
+    assert checked > 40
