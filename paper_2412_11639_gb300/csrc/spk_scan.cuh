@@ -207,7 +207,39 @@ struct TreeScan {
         bad = 0;
     }
     SPK_DEV void first_spike(int t) { last_t = t; }
-    SPK_DEV bool absorb_ones(int) { return false; }
+
+    // 32 spikes at steps base .. base+31 (an all-ones time word): 32 intervals of 1.  If the
+    // path of value 1 is steady -- every node on it already holds 1 in its open sequence
+    // and (above the last level) its previous element was a 1 as well, so that each of the
+    // 32 elements sends a distance of 1 one level down -- no node can break, and the word
+    // is absorbed in O(levels).  Otherwise nothing changes and false is returned.
+    SPK_DEV bool absorb_ones(int base) {
+        if (last_t != base - 1) return false;
+        int path[TREE_MAX];
+        int k = 0, levels = 0;
+        for (int level = 1;; ++level) {
+            if (cnt[k] == 0 || (v0[k] != 1 && v1[k] != 1)) return false;
+            path[levels++] = k;
+            if (level >= n) break;
+            const int b = v0[k] == 1 ? 0 : 1;
+            if ((b ? q1[k] : q0[k]) != jn[k] - 1) return false;
+            k = 2 * k + 1 + b;
+        }
+        for (int m = 0; m < levels; ++m) {
+            const int kk = path[m];
+            jn[kk] += 32;
+            cnt[kk] += 32;
+            pct[kk] = base + 31;
+            pci[kk] = nint + 31;
+            if (m + 1 < levels) {
+                if (v0[kk] == 1) q0[kk] = jn[kk] - 1;
+                else q1[kk] = jn[kk] - 1;
+            }
+        }
+        nint += 32;
+        last_t = base + 31;
+        return true;
+    }
 
     SPK_DEV int frontier() const {
         int S = last_t;
