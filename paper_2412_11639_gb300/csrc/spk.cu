@@ -7,14 +7,17 @@
 //      frame-major bits into per-pixel time sequences);
 //   2. each compute warp turns its 32 x 32 bit tile (32 steps x 32 pixels) into one
 //      32-step time word per lane with a 5-stage shuffle transpose;
-//   3. each lane runs the FSR / SSR stability scan (spk_scan.cuh) over the spikes of its
-//      time word (ffs per spike) and receives final stable sequences in time order;
-//   4. a sequence whose span covers new frame samples becomes a record
-//      (last frame index, value = threshold * N / D, Eq. 4) in a per-lane shared-memory
-//      queue -- the analogue of the FPGA encoder's (duration, intensity) records;
-//   5. after every 32 steps the warp writes the frame rows every lane has resolved, one
+//   3. each lane runs the stability scan (spk_scan.cuh: FSR, SSR, the TFI baseline, or
+//      the general n-order tree) over the spikes of its time word (ffs per spike) and
+//      hands every cut to a per-lane shared-memory queue;
+//   4. final cuts are converted in place into records (last frame index, value =
+//      threshold * N / D, Eq. 4) -- the analogue of the FPGA encoder's (duration,
+//      intensity) records;
+//   5. every 256 steps the warp writes the frame rows every lane has resolved, one
 //      coalesced row (32 consecutive pixels) per store; a lane whose queue runs full
 //      writes its oldest record on its own.
+// The TFP baseline and the refiner's input features use the same pipeline in kernels of
+// their own; the learned refiner lives in refiner.cu.
 // Values are known only when a sequence closes, which may be thousands of steps later
 // (a static pixel is one sequence), so rows are written when resolved, not when sampled.
 #include <cuda.h>
@@ -24,7 +27,6 @@
 #include <cudaTypedefs.h>
 
 #include <climits>
-#include <type_traits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -32,6 +34,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 
 #include "../../include/spk.h"
 #include "spk_scan.cuh"
