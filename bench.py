@@ -327,16 +327,27 @@ def run_ours(args, rank, world, local_rank):
     # end to end through the public C ABI with pinned host buffers (copies timed)
     e2e = None
     if args.e2e_steps > 0:
+        # every step copies its input from pinned host memory and its frames back; the calls
+        # are asynchronous and alternate between two lanes, so that a step's device-to-host
+        # copy overlaps the next step's input copy and scan
         h_in = torch.from_numpy(st).pin_memory()
-        h_out = torch.empty((w.T_out, w.H, w.W), dtype=dtype).pin_memory()
-        spk.spk_reconstruct_host(R.ctx, h_in, w.H, w.W, w.T, 1.0, h_out)
+        h_out = [torch.empty((w.T_out, w.H, w.W), dtype=dtype).pin_memory() for _ in range(2)]
+        for k in range(2):
+            spk.spk_reconstruct_host_async(R.ctx, h_in, w.H, w.W, w.T, 1.0, h_out[k])
+        spk.spk_synchronize(R.ctx)
         barrier(world)
         te0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            spk.spk_reconstruct_host(R.ctx, h_in, w.H, w.W, w.T, 1.0, h_out)
+        for k in range(args.e2e_steps):
+            spk.spk_reconstruct_host_async(R.ctx, h_in, w.H, w.W, w.T, 1.0, h_out[k % 2])
+        spk.spk_synchronize(R.ctx)
         te_dt = max_over_ranks(time.perf_counter() - te0, world)
+        t1 = time.perf_counter()
+        spk.spk_reconstruct_host(R.ctx, h_in, w.H, w.W, w.T, 1.0, h_out[0])
+        one_call = time.perf_counter() - t1
         e2e = {"value": w.P * w.T_out * args.e2e_steps * world / te_dt / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(st.nbytes), "d2h_bytes_per_step": int(h_out.numel() * esz)}
+               "h2d_bytes_per_step": int(st.nbytes), "d2h_bytes_per_step": int(h_out[0].numel() * esz),
+               "api": "spk_reconstruct_host_async x steps, then spk_synchronize",
+               "single_call_ms": one_call * 1e3}
     R.close()
 
     refined = None

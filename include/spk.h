@@ -111,6 +111,17 @@ int spk_reconstruct(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, fl
 int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W, int T,
                          float threshold, void *host_frames);
 
+/* Asynchronous spk_reconstruct_host: enqueues the host-to-device copy of the stream, the
+ * reconstruction and the device-to-host copy of the frames, and returns.  Consecutive calls
+ * alternate between two internal lanes (a stream and a pair of device buffers each, grown
+ * on demand), so that one call's device-to-host copy overlaps the next call's input copy and
+ * scan.  Work already enqueued on ctx's stream is ordered before the call.  host_stream and
+ * host_frames must stay untouched until spk_synchronize(ctx) returns; it waits for every
+ * call and reports device errors.  Pinned host memory keeps the copies asynchronous.
+ * Errors: as spk_reconstruct_host. */
+int spk_reconstruct_host_async(spk_ctx *ctx, const uint8_t *host_stream, int H, int W, int T,
+                               float threshold, void *host_frames);
+
 /* A live stream: pushed piece by piece (spk_run), with its per-pixel scan state resident
  * in device memory between pieces, so that pieces arriving over time give exactly the
  * frames of one spk_reconstruct over the whole stream.  The FPGA of Sec. III-C carries the

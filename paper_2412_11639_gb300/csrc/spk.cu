@@ -825,6 +825,14 @@ struct spk_ctx {
     size_t out_cap;
     int64_t launches;
     int tile;        // time tile of the frames kernels: 32, 64 or 128 steps
+    // spk_reconstruct_host_async: two lanes, each a stream with its own staging buffers
+    cudaStream_t lane_stream[2];
+    uint8_t *lane_in[2];
+    size_t lane_in_cap[2];
+    void *lane_out[2];
+    size_t lane_out_cap[2];
+    cudaEvent_t lane_fence;  // orders the work already on `stream` before a lane's call
+    int next_lane;
     char msg[512];
 };
 
@@ -1083,6 +1091,15 @@ int spk_destroy(spk_ctx *ctx) {
     if (!ctx) return SPK_OK;
     cudaSetDevice(ctx->cfg.device);
     cudaStreamSynchronize(ctx->stream);
+    for (int l = 0; l < 2; ++l) {
+        if (ctx->lane_stream[l]) {
+            cudaStreamSynchronize(ctx->lane_stream[l]);
+            cudaStreamDestroy(ctx->lane_stream[l]);
+        }
+        if (ctx->lane_in[l]) cudaFree(ctx->lane_in[l]);
+        if (ctx->lane_out[l]) cudaFree(ctx->lane_out[l]);
+    }
+    if (ctx->lane_fence) cudaEventDestroy(ctx->lane_fence);
     cudaFree(ctx->d_status);
     if (ctx->d_in) cudaFree(ctx->d_in);
     if (ctx->d_out) cudaFree(ctx->d_out);
@@ -1130,6 +1147,8 @@ int spk_synchronize(spk_ctx *ctx) {
     if (!ctx) return SPK_ERR_ARG;
     cudaSetDevice(ctx->cfg.device);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    for (int l = 0; l < 2 && e == cudaSuccess; ++l)
+        if (ctx->lane_stream[l]) e = cudaStreamSynchronize(ctx->lane_stream[l]);
     if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
     int st = 0;
     if (cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -1404,6 +1423,62 @@ int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W,
     if (cudaMemcpyAsync(host_frames, ctx->d_out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
         return fail(ctx, SPK_ERR_CUDA, "D2H copy: %s", cudaGetErrorString(cudaGetLastError()));
     return spk_synchronize(ctx);
+}
+
+int spk_reconstruct_host_async(spk_ctx *ctx, const uint8_t *host_stream, int H, int W, int T, float threshold,
+                               void *host_frames) {
+    int rc = check_stream_args(ctx, host_stream, H, W, T, threshold);
+    if (rc) return rc;
+    ctx->msg[0] = 0;
+    if (!host_frames) return fail(ctx, SPK_ERR_ARG, "host_frames is NULL");
+    const int64_t P = static_cast<int64_t>(H) * W;
+    const int64_t T_out = spk_num_frames(T, ctx->cfg.frame_stride);
+    const size_t esz = ctx->cfg.out_dtype == SPK_F16 ? 2 : 4;
+    const size_t out_bytes = static_cast<size_t>(T_out) * static_cast<size_t>(P) * esz;
+    const size_t in_bytes = static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W));
+    cudaSetDevice(ctx->cfg.device);
+    const int l = ctx->next_lane;
+    if (!ctx->lane_stream[l] && cudaStreamCreateWithFlags(&ctx->lane_stream[l], cudaStreamNonBlocking) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "cudaStreamCreate failed");
+    if (!ctx->lane_fence && cudaEventCreateWithFlags(&ctx->lane_fence, cudaEventDisableTiming) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "cudaEventCreate failed");
+    cudaStream_t ls = ctx->lane_stream[l];
+    // a lane's buffers grow on demand; cudaFree waits for the lane's earlier work
+    if (in_bytes > ctx->lane_in_cap[l]) {
+        if (ctx->lane_in[l]) cudaFree(ctx->lane_in[l]);
+        ctx->lane_in[l] = nullptr;
+        ctx->lane_in_cap[l] = 0;
+        if (cudaMalloc(&ctx->lane_in[l], in_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) failed", in_bytes);
+        }
+        ctx->lane_in_cap[l] = in_bytes;
+    }
+    if (out_bytes > ctx->lane_out_cap[l]) {
+        if (ctx->lane_out[l]) cudaFree(ctx->lane_out[l]);
+        ctx->lane_out[l] = nullptr;
+        ctx->lane_out_cap[l] = 0;
+        if (cudaMalloc(&ctx->lane_out[l], out_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) failed", out_bytes);
+        }
+        ctx->lane_out_cap[l] = out_bytes;
+    }
+    if (cudaEventRecord(ctx->lane_fence, ctx->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(ls, ctx->lane_fence, 0) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "stream ordering: %s", cudaGetErrorString(cudaGetLastError()));
+    if (cudaMemcpyAsync(ctx->lane_in[l], host_stream, in_bytes, cudaMemcpyHostToDevice, ls) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "H2D copy: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaStream_t own = ctx->stream;  // the scan launches on the lane
+    ctx->stream = ls;
+    rc = run_scan(ctx, ctx->lane_in[l], H, W, T, threshold, ctx->lane_out[l], nullptr, nullptr, nullptr, nullptr,
+                  nullptr, 0, false);
+    ctx->stream = own;
+    if (rc) return rc;
+    if (cudaMemcpyAsync(host_frames, ctx->lane_out[l], out_bytes, cudaMemcpyDeviceToHost, ls) != cudaSuccess)
+        return fail(ctx, SPK_ERR_CUDA, "D2H copy: %s", cudaGetErrorString(cudaGetLastError()));
+    ctx->next_lane = l ^ 1;
+    return SPK_OK;
 }
 
 }  // extern "C"

@@ -23,7 +23,7 @@ EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reco
            "spk_get_tile", "spk_autotune", "spk_features", "spk_refiner_num_params",
            "spk_refiner_create", "spk_refiner_destroy", "spk_refiner_last_error",
            "spk_refiner_set_params", "spk_refiner_get_params", "spk_refiner_forward",
-           "spk_refiner_train_step", "spk_refiner_synchronize")
+           "spk_refiner_train_step", "spk_refiner_synchronize", "spk_reconstruct_host_async")
 SPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -69,6 +69,8 @@ def load(path: str | None = None):
     lib.spk_reconstruct.restype = i32
     lib.spk_reconstruct_host.argtypes = [vp, vp, i32, i32, i32, f32, vp]
     lib.spk_reconstruct_host.restype = i32
+    lib.spk_reconstruct_host_async.argtypes = [vp, vp, i32, i32, i32, f32, vp]
+    lib.spk_reconstruct_host_async.restype = i32
     lib.spk_segments.argtypes = [vp, vp, i32, i32, i32, f32, vp, vp, vp, vp, vp, i32]
     lib.spk_segments.restype = i32
     lib.spk_synchronize.argtypes = [vp]
@@ -299,3 +301,9 @@ def spk_refiner_train_step(r, stream, x0, plain, gt, N, H, W, lr, want_loss=True
 
 def spk_refiner_synchronize(r, stream=None):
     return _rcheck(r, load().spk_refiner_synchronize(r, stream))
+
+
+def spk_reconstruct_host_async(ctx, host_stream, H, W, T, threshold, host_frames):
+    """Enqueue a host-buffer reconstruction (copies included); spk_synchronize(ctx) waits."""
+    return _check(ctx, load().spk_reconstruct_host_async(ctx, _addr(host_stream), H, W, T, threshold,
+                                                         _addr(host_frames)))

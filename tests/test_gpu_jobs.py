@@ -191,3 +191,22 @@ def test_batch_captured_in_cuda_graph_and_autotuned(env):
         for o, ref in zip(outs, refs):
             assert np.array_equal(o.cpu().numpy().view(np.uint32), ref.view(np.uint32)), tile
     R.close()
+
+
+def test_host_async_lanes_equal_sync(env):
+    """Asynchronous host calls alternate between two lanes; each result equals the
+    synchronous call on the same input."""
+    torch, pkg = env
+    from paper_2412_11639_gb300 import spk
+    ws = [spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=33, W=70, T=2500, seed=s) for s in (5, 6, 7)]
+    sts = [torch.from_numpy(spkgen.make_stream(w)[0]).pin_memory() for w in ws]
+    R = pkg.Reconstructor(order=2, stride=10)
+    outs = [torch.empty((ws[0].T_out, 33, 70), dtype=torch.float32).pin_memory() for _ in ws]
+    for st, o in zip(sts, outs):
+        spk.spk_reconstruct_host_async(R.ctx, st, 33, 70, 2500, 1.0, o)
+    spk.spk_synchronize(R.ctx)
+    for st, o in zip(sts, outs):
+        ref = torch.empty_like(o)
+        spk.spk_reconstruct_host(R.ctx, st, 33, 70, 2500, 1.0, ref)
+        assert torch.equal(o, ref)
+    R.close()
