@@ -10,12 +10,13 @@ from . import spk
 from .build import build
 from .spk import (SPK_F16, SPK_F32, SpkError, spk_create, spk_destroy, spk_launch_count,
                   spk_last_error, spk_num_frames, spk_pitch, spk_reconstruct,
-                  spk_reconstruct_host, spk_run, spk_segments, spk_stream_close,
-                  spk_stream_open, spk_stream_ready, spk_stream_steps, spk_synchronize)
+                  spk_reconstruct_host, spk_reconstruct_host_async, spk_run, spk_segments,
+                  spk_stream_close, spk_stream_open, spk_stream_ready, spk_stream_steps,
+                  spk_synchronize)
 
 __all__ = ["spk", "build", "Reconstructor", "SpkError", "SPK_F32", "SPK_F16", "spk_create",
            "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
-           "spk_reconstruct_host", "spk_segments", "spk_synchronize", "spk_last_error",
+           "spk_reconstruct_host", "spk_reconstruct_host_async", "spk_segments", "spk_synchronize", "spk_last_error",
            "spk_launch_count", "spk_run", "spk_stream_open", "spk_stream_close",
            "spk_stream_ready", "spk_stream_steps", "Stream"]
 
