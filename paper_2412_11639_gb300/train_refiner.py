@@ -19,8 +19,8 @@ def main(argv=None):
     ap.add_argument("--clips", type=int, default=10000)
     ap.add_argument("--steps-per-clip", type=int, default=2)
     ap.add_argument("--batch", type=int, default=16)
-    ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--lr-final", type=float, default=1e-4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-final", type=float, default=5e-5)
     ap.add_argument("--T", type=int, default=2000)
     ap.add_argument("--seed", type=int, default=0, help="initial weights")
     ap.add_argument("--out", default=None)
