@@ -42,6 +42,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dynamic_250x400x20000")
+    ap.add_argument("--T", type=int, default=0,
+                    help="cut the workload to its first T steps (profiling a smaller case)")
     ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="method: 1 FSR, 2 SSR (default), 3 TFI, 4 TFP (window --tfp-window), "
                          "5 the n-order tree (--stability-order levels)")
@@ -150,17 +152,19 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------- inputs ----
-def workload_stream(name: str, rank: int, world: int, device: int | None = None):
+def workload_stream(name: str, rank: int, world: int, device: int | None = None, T_cut: int = 0):
     """The workload's packed stream as a host array: made by the GPU generator when a device
     is given (the same bits as the C generator), else by the C generator (rank 0, cached in
     the temp dir)."""
     import numpy as np
     import spkgen
     w = spkgen.WORKLOADS[name]
+    if T_cut:
+        w = w.resized(T=T_cut, name=f"{w.name}[:{T_cut}]")
     if device is not None:
         st, _ = spkgen.make_stream_cuda(w, device=device)
         return w, st.cpu().numpy()
-    cache = os.path.join(tempfile.gettempdir(), f"spk_stream_{name}.npy")
+    cache = os.path.join(tempfile.gettempdir(), f"spk_stream_{name}_{w.T}.npy")
     if rank == 0 and not os.path.exists(cache):
         st, _ = spkgen.make_stream(w)
         tmp = cache + f".{os.getpid()}.tmp.npy"
@@ -232,7 +236,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     import numpy as np
-    w, st = workload_stream(args.workload, 0, 1)
+    w, st = workload_stream(args.workload, 0, 1, T_cut=args.T)
     chunk = 1024
     starts = np.arange(0, w.P, chunk)
     for i in range(args.warmup):
@@ -282,7 +286,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_2412_11639_gb300 import spk
 
     torch.cuda.set_device(local_rank)
-    w, st = workload_stream(args.workload, rank, world, device=local_rank)
+    w, st = workload_stream(args.workload, rank, world, device=local_rank, T_cut=args.T)
     dtype = torch.float16 if w.out_dtype == "f16" else torch.float32
     esz = 2 if dtype == torch.float16 else 4
     R = pkg.Reconstructor(order=args.order, stride=w.stride, dtype=dtype, device=local_rank,
