@@ -112,3 +112,11 @@ def test_refiner_host_checks(lib):
         with pytest.raises(spk.SpkError) as e:
             spk.spk_refiner_create(0, 1)
         assert e.value.code == spk.SPK_ERR_CUDA
+
+
+def test_packaged_refiner_checkpoint():
+    import numpy as np
+    from paper_2412_11639_gb300 import refiner
+    p = np.load(refiner.CHECKPOINT)
+    assert p.dtype == np.float32 and p.shape == (spk.spk_refiner_num_params(),)
+    assert np.isfinite(p).all() and np.abs(p).max() < 10

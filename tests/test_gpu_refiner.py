@@ -205,3 +205,30 @@ def test_training_beats_plain_on_held_out_stream():
     assert p_ref > p_plain + 0.3
     assert s_ref > s_plain
     ref.close()
+
+
+def test_packaged_checkpoint_matches_reference_on_a_scene():
+    """The whole refiner path with the trained weights (features on the GPU, tcgen05
+    forward) against the PyTorch restatement on the same features: same frames within the
+    forward tolerance, and the refined frames beat the plain ones."""
+    w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=40, W=150, T=3000)
+    rec = pkg.Reconstructor(order=2, stride=w.stride)
+    stream, gt = spkgen.make_stream(w, gt_stride=w.stride)
+    dev = torch.from_numpy(stream).cuda()
+    plain = rec(dev, w.H, w.W, w.T)
+    x0 = refiner.features(rec, dev, w.H, w.W, w.T, plain)
+    ref = refiner.Refiner()
+    ref.load(refiner.CHECKPOINT)
+    out = ref(x0, plain)
+    spk.spk_refiner_synchronize(ref.r, ref.stream.cuda_stream)
+    # the restatement reads the GPU's features back in NHWC order
+    xh = x0.float().cpu().numpy().transpose(0, 1, 3, 2, 4).reshape(w.T_out, w.H, w.W, 16)
+    p = ref.params()
+    want, _, _ = refnet.forward(p, xh, plain.cpu().numpy())
+    got = out.cpu().numpy()
+    corr = np.abs(want - plain.cpu().numpy()).max()
+    assert np.abs(got - want).max() <= 1e-2 * corr + 1e-6
+    g = gt.reshape(w.T_out, w.H, w.W)[20:]
+    assert quality.psnr(got[20:], g) > quality.psnr(plain.cpu().numpy()[20:], g) + 2.0
+    ref.close()
+    rec.close()
