@@ -117,7 +117,7 @@ def simulator_clip(rec, w, device: int = 0):
 
 
 def train_on_simulator(ref: Refiner, rec, base, n_clips: int, steps_per_clip: int = 4, batch: int = 16,
-                       lr: float = 2e-3, lr_final: float = 2e-4, seed0: int = 1000, log=None):
+                       lr: float = 1e-3, lr_final: float = 5e-5, seed0: int = 1000, log=None):
     """Train on n_clips freshly simulated clips of recipe `base` (seeds seed0, seed0+1, ...),
     steps_per_clip Adam steps of `batch` consecutive frames each, learning rate decaying
     linearly from lr to lr_final.  Returns the mean loss of every clip's steps."""
