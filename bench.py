@@ -393,7 +393,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
-                     "kernel": KERNEL, "kernel_ms": kern_ms,
+                     "kernel": "spk_tfp_kernel" if args.order == 4 else KERNEL, "kernel_ms": kern_ms,
                      "algorithmic_bytes_per_launch": alg_bytes},
         "cpu_baseline": cpu,
         "e2e": e2e,
