@@ -269,6 +269,12 @@ int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const f
  * loss_host performs the same check. */
 int spk_refiner_synchronize(spk_refiner *r, void *stream);
 
+/* Test hook of the failure paths (no counterpart in the paper): the library's next n device
+ * allocations (contexts, stream states, host-call staging buffers) fail as if the device
+ * were out of memory, so that the SPK_ERR_OOM paths can be exercised without exhausting a
+ * shared GPU.  n = 0 clears it.  Errors: SPK_ERR_ARG for n < 0. */
+int spk_debug_fail_allocations(int n);
+
 /* Diagnostic of the bounded device waits (no counterpart in the paper).  Every wait of
  * the kernels (the mbarrier waits of the stream pipeline) gives up after a bounded time
  * (about 2 s) instead of hanging, sets the timeout bit of the context's status word and

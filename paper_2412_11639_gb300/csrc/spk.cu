@@ -32,6 +32,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <type_traits>
@@ -815,6 +816,23 @@ struct spk_stream {
     int *d_ready;    // min over pixels of frames written, after the last push
 };
 
+// Device allocations of the library go through dev_malloc, which a test hook can make fail
+// (spk_debug_fail_allocations) to exercise the SPK_ERR_OOM paths without exhausting a GPU.
+namespace {
+std::atomic<int> g_fail_allocs{0};
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    int n = g_fail_allocs.load();
+    while (n > 0 && !g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n > 0) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+}  // namespace
+
 struct spk_ctx {
     spk_config cfg;
     cudaStream_t stream;
@@ -1073,7 +1091,7 @@ int spk_create(spk_ctx **out, const spk_config *cfg) {
     c->cfg = *cfg;
     c->stream = static_cast<cudaStream_t>(cfg->stream);
     c->tile = TT_DEFAULT;
-    if (cudaMalloc(&c->d_status, 16) != cudaSuccess) {
+    if (dev_malloc(&c->d_status, 16) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return fail(nullptr, SPK_ERR_OOM, "cudaMalloc of the status word failed");
@@ -1178,7 +1196,7 @@ int spk_stream_open(spk_ctx *ctx, int H, int W, int T, spk_stream **out) {
     st->T = T;
     st->device = ctx->cfg.device;
     const size_t carry_bytes = static_cast<size_t>(CARRY_INTS) * static_cast<size_t>(H) * static_cast<size_t>(W) * 4;
-    if (cudaMalloc(&st->d_carry, carry_bytes) != cudaSuccess || cudaMalloc(&st->d_ready, sizeof(int)) != cudaSuccess) {
+    if (dev_malloc(&st->d_carry, carry_bytes) != cudaSuccess || dev_malloc(&st->d_ready, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         if (st->d_carry) cudaFree(st->d_carry);
         delete st;
@@ -1399,7 +1417,7 @@ int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W,
         if (ctx->d_in) cudaFree(ctx->d_in);
         ctx->d_in = nullptr;
         ctx->in_cap = 0;
-        if (cudaMalloc(&ctx->d_in, in_bytes) != cudaSuccess) {
+        if (dev_malloc(&ctx->d_in, in_bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) failed", in_bytes);
         }
@@ -1409,7 +1427,7 @@ int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W,
         if (ctx->d_out) cudaFree(ctx->d_out);
         ctx->d_out = nullptr;
         ctx->out_cap = 0;
-        if (cudaMalloc(&ctx->d_out, out_bytes) != cudaSuccess) {
+        if (dev_malloc(&ctx->d_out, out_bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) failed", out_bytes);
         }
@@ -1423,6 +1441,12 @@ int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W,
     if (cudaMemcpyAsync(host_frames, ctx->d_out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
         return fail(ctx, SPK_ERR_CUDA, "D2H copy: %s", cudaGetErrorString(cudaGetLastError()));
     return spk_synchronize(ctx);
+}
+
+int spk_debug_fail_allocations(int n) {
+    if (n < 0) return SPK_ERR_ARG;
+    g_fail_allocs.store(n);
+    return SPK_OK;
 }
 
 int spk_reconstruct_host_async(spk_ctx *ctx, const uint8_t *host_stream, int H, int W, int T, float threshold,
@@ -1448,7 +1472,7 @@ int spk_reconstruct_host_async(spk_ctx *ctx, const uint8_t *host_stream, int H, 
         if (ctx->lane_in[l]) cudaFree(ctx->lane_in[l]);
         ctx->lane_in[l] = nullptr;
         ctx->lane_in_cap[l] = 0;
-        if (cudaMalloc(&ctx->lane_in[l], in_bytes) != cudaSuccess) {
+        if (dev_malloc(&ctx->lane_in[l], in_bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) failed", in_bytes);
         }
@@ -1458,7 +1482,7 @@ int spk_reconstruct_host_async(spk_ctx *ctx, const uint8_t *host_stream, int H, 
         if (ctx->lane_out[l]) cudaFree(ctx->lane_out[l]);
         ctx->lane_out[l] = nullptr;
         ctx->lane_out_cap[l] = 0;
-        if (cudaMalloc(&ctx->lane_out[l], out_bytes) != cudaSuccess) {
+        if (dev_malloc(&ctx->lane_out[l], out_bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) failed", out_bytes);
         }

@@ -23,7 +23,8 @@ EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reco
            "spk_get_tile", "spk_autotune", "spk_features", "spk_refiner_num_params",
            "spk_refiner_create", "spk_refiner_destroy", "spk_refiner_last_error",
            "spk_refiner_set_params", "spk_refiner_get_params", "spk_refiner_forward",
-           "spk_refiner_train_step", "spk_refiner_synchronize", "spk_reconstruct_host_async")
+           "spk_refiner_train_step", "spk_refiner_synchronize", "spk_reconstruct_host_async",
+           "spk_debug_fail_allocations")
 SPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -115,6 +116,8 @@ def load(path: str | None = None):
     lib.spk_refiner_train_step.restype = i32
     lib.spk_refiner_synchronize.argtypes = [vp, vp]
     lib.spk_refiner_synchronize.restype = i32
+    lib.spk_debug_fail_allocations.argtypes = [i32]
+    lib.spk_debug_fail_allocations.restype = i32
     lib.spk_selftest_wait.argtypes = [vp, i64]
     lib.spk_selftest_wait.restype = i32
     lib.spk_reconstruct_host_noalloc.argtypes = [_c.POINTER(spk_config), vp, i32, i32, i32, f32, vp]
@@ -307,3 +310,8 @@ def spk_reconstruct_host_async(ctx, host_stream, H, W, T, threshold, host_frames
     """Enqueue a host-buffer reconstruction (copies included); spk_synchronize(ctx) waits."""
     return _check(ctx, load().spk_reconstruct_host_async(ctx, _addr(host_stream), H, W, T, threshold,
                                                          _addr(host_frames)))
+
+
+def spk_debug_fail_allocations(n: int):
+    """Make the library's next n device allocations fail (test hook of the SPK_ERR_OOM paths)."""
+    return _check(None, load().spk_debug_fail_allocations(n))
