@@ -531,11 +531,13 @@ def run_refine(args):
 
 # ------------------------------------------------------------- extra modes ----
 def _distinct_streams(specs):
+    """Moving-scene streams of the given sizes and seeds, made by the GPU generator (the
+    same bits as the C generator), as host arrays."""
     import spkgen
     out = []
     for (H, W, T, seed) in specs:
         w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=H, W=W, T=T, seed=seed)
-        out.append((H, W, T, spkgen.make_stream(w)[0]))
+        out.append((H, W, T, spkgen.make_stream_cuda(w)[0].cpu().numpy()))
     return out
 
 
@@ -547,8 +549,11 @@ def run_batch(args):
     import paper_2412_11639_gb300 as pkg
     from paper_2412_11639_gb300 import spk
     rng = np.random.default_rng(11)
-    specs = [(int(rng.integers(128, 513)), int(rng.integers(128, 513)), int(rng.integers(2000, 20001)), 40 + k)
+    # sizes from 128 x 128 to 1000 x 1000 (both ends included), lengths 2000 .. 20000 steps
+    specs = [(int(rng.integers(128, 1001)), int(rng.integers(128, 1001)), int(rng.integers(2000, 20001)), 40 + k)
              for k in range(6)]
+    specs[0] = (128, 128) + specs[0][2:]
+    specs[-1] = (1000, 1000) + specs[-1][2:]
     distinct = _distinct_streams(specs)
     side = torch.cuda.Stream()
     R = pkg.Reconstructor(order=args.order, stride=10, dtype=torch.float16, stream=side)
