@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CU
             int n, x0, y0, y1;
             geometry(task, n, x0, y0, y1);
             for (int r = y0 - 1; r <= y1; ++r) {
-                // the slot's previous row must have been released (from the second round on)
+                // the slot's previous row must have been released (from the second pass over the ring on)
                 bool go = true;
                 if (lane == 0) {
                     if (issued >= RING) go = mbar_wait(&empty[sl], ph ^ 1, status);
