@@ -14,12 +14,15 @@ time and then produces `rate` steps per second.  The server
   stream;
 * records, for every frame, the latency from the moment its sampling step was produced to
   the moment the frame became final for every pixel (a frame is final once the stable
-  span covering it closes -- for a static pixel that can be the end of the stream).
+  span covering it closes -- for a static pixel that can be the end of the stream);
+* lets any thread cancel a request (cancel(rid)): a waiting request is dropped, an active
+  one gives back its slot, its device state and its memory at the next tick.
 
 The scheduling is host logic; every step of the reconstruction runs in libspk.
 """
 from __future__ import annotations
 
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -66,6 +69,7 @@ class ServeStats:
     max_ms: float
     peak_active: int
     admitted_late_s: float   # total time requests waited for admission
+    cancelled: int = 0       # requests cancelled before they finished
 
 
 class Server:
@@ -80,6 +84,13 @@ class Server:
         self.esz = 2 if self.rec.dtype == torch.float16 else 4
         self.mem_budget, self.max_streams, self.max_piece = mem_budget, max_streams, max_piece
         self.results = {}        # rid -> frames (device tensor [T_out][H][W])
+        self._cancel = set()
+        self._lock = threading.Lock()
+
+    def cancel(self, rid: int):
+        """Cancel request rid (from any thread); it leaves at the loop's next tick."""
+        with self._lock:
+            self._cancel.add(rid)
 
     def mem_needed(self, r: Request) -> int:
         P = r.H * r.W
@@ -100,8 +111,23 @@ class Server:
         busy = 0.0
         lat_all = []
         pinned = {r.rid: torch.from_numpy(r.stream).pin_memory() for r in pending}  # camera buffers
+        cancelled = 0
         t0 = clock()
         while pending or active:
+            with self._lock:
+                drop, self._cancel = self._cancel, set()
+            if drop:
+                for r in [p for p in pending if p.rid in drop]:
+                    pending.remove(r)
+                    pinned.pop(r.rid, None)
+                    cancelled += 1
+                for a in [x for x in active if x.req.rid in drop]:
+                    a.s.close()                  # waits for its last launch, frees its state
+                    used -= a.mem
+                    active.remove(a)
+                    cancelled += 1
+            if not (pending or active):
+                break
             now = clock() - t0
             # admission, first come first served, by memory and slots
             while (pending and pending[0].arrival <= now and len(active) < self.max_streams
@@ -155,7 +181,8 @@ class Server:
         frames = int(sum(v.shape[0] for v in self.results.values()))
         pf = int(sum(v.shape[0] * v.shape[1] * v.shape[2] for v in self.results.values()))
         return ServeStats(frames, pf, wall, busy, launches, float(np.percentile(lat, 50) * 1e3),
-                          float(np.percentile(lat, 99) * 1e3), float(lat.max() * 1e3), peak, waited)
+                          float(np.percentile(lat, 99) * 1e3), float(lat.max() * 1e3), peak, waited,
+                          cancelled)
 
     def close(self):
         self.rec.close()

@@ -39,3 +39,39 @@ def test_served_results_equal_alone():
         assert torch.equal(got.view(torch.int32), alone.view(torch.int32)), r.rid
     R.close()
     srv.close()
+
+
+def test_cancelled_requests_leave_and_the_rest_is_unchanged():
+    """A request cancelled while waiting never runs; one cancelled while active gives its
+    slot and state back at the next tick; every other result still equals its stream alone."""
+    import threading
+
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_11639_gb300 as pkg
+    from paper_2412_11639_gb300.serving import Request, Server
+    pkg.build()
+    rng = np.random.default_rng(8)
+    reqs = []
+    for k in range(6):
+        H, W, T = int(rng.integers(8, 32)), int(rng.integers(16, 64)), int(rng.integers(500, 2500))
+        w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=H, W=W, T=T, seed=200 + k)
+        st, _ = spkgen.make_stream(w)
+        rate = 1.0e4 if k == 0 else 2.0e5               # request 0 runs for 50-250 ms
+        reqs.append(Request(k, st, H, W, arrival=0.002 * k if k < 5 else 0.4, rate=rate))
+    srv = Server(order=2, stride=3, max_streams=4, max_piece=256)
+    srv.cancel(5)                                      # still waiting: dropped
+    timer = threading.Timer(0.03, srv.cancel, args=(0,))  # active by then: leaves mid-stream
+    timer.start()
+    stats = srv.run(reqs)
+    timer.join()
+    assert stats.cancelled == 2
+    assert 0 not in srv.results and 5 not in srv.results
+    R = pkg.Reconstructor(order=2, stride=3)
+    for r in reqs[1:5]:
+        alone = R(torch.from_numpy(r.stream).cuda(), r.H, r.W, r.T, 1.0)
+        R.synchronize()
+        assert torch.equal(srv.results[r.rid].view(torch.int32), alone.view(torch.int32)), r.rid
+    R.close()
+    srv.close()
