@@ -188,9 +188,10 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-constexpr int RING = 5;  // input-row slots
-constexpr int TMA_PX = 32;                  // pixels per TMA box (256 bf16: the largest box edge)
-constexpr int HALO_PX = 5 * TMA_PX;         // pixels loaded per halo row (>= 130)
+constexpr int RING = 6;  // input-row slots
+constexpr int TMA_PX = 32;                  // pixels per main TMA box (256 bf16: the largest box edge)
+constexpr int TAIL_PX = 8;                  // pixels of the last box of a plane (pixels 128 .. 135)
+constexpr int HALO_PX = 4 * TMA_PX + TAIL_PX;  // pixels loaded per halo row (>= 130), 136 x 16 B = 17 x 128 B
 constexpr int NACC = 4;  // accumulators in tensor memory
 
 template <int CI, int CO>
@@ -212,6 +213,7 @@ struct ConvSmem {
 // warp 5 (one thread) issues the MMAs, and allocates / frees the tensor memory.
 template <int CI, int CO, int MODE>
 __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CUtensorMap xmap,
+                                                      const __grid_constant__ CUtensorMap xmap_tail,
                                                       const bf16 *__restrict__ Wt, const float *__restrict__ bias,
                                                       void *Y, const bf16 *__restrict__ mask,
                                                       const float *__restrict__ resid, int N, int H, int W,
@@ -276,9 +278,12 @@ __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CU
 
     if (warp == 4) {  // ------------------------------------------------ TMA producer ----
         // lane 0 waits for the slot and arms its barrier; then CH x 5 lanes issue one box each
-        constexpr int BOXES = CH * (HALO_PX / TMA_PX);
+        constexpr int BOXES = CH * 5;  // four boxes of 32 pixels and one of 8 per chunk plane
         static_assert(BOXES <= 32, "one box per lane");
-        if (lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap_tail)) : "memory");
+        }
         int sl = 0, ph = 0, issued = 0;  // ring slot, its phase, loads issued (the same in every lane)
         bool ok = true;
         for (int64_t task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
@@ -296,9 +301,9 @@ __global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CU
                     break;
                 }
                 if (lane < BOXES) {
-                    const int ch = lane / (HALO_PX / TMA_PX), j = lane % (HALO_PX / TMA_PX);
-                    tma_load_4d(sbase + sl * L::SLOT + ch * L::PLANE + j * TMA_PX * 16, &xmap, &full[sl],
-                                (x0 - 1 + j * TMA_PX) * 8, ch, r, n);
+                    const int ch = lane / 5, j = lane % 5;
+                    tma_load_4d(sbase + sl * L::SLOT + ch * L::PLANE + j * TMA_PX * 16, j < 4 ? &xmap : &xmap_tail,
+                                &full[sl], (x0 - 1 + j * TMA_PX) * 8, ch, r, n);
                 }
                 ++issued;
                 if (++sl == RING) sl = 0, ph ^= 1;
@@ -464,14 +469,14 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 // halo-row loads of a [N][H][C/8][W][8] bf16 tensor viewed as (W*8, C/8, H, N): boxes of
 // 256 elements (32 pixels) of one chunk plane, so every TMA request moves 512 contiguous bytes
-bool make_xmap(CUtensorMap *map, const bf16 *X, int C, int N, int H, int W) {
+bool make_xmap(CUtensorMap *map, const bf16 *X, int C, int N, int H, int W, int box_px) {
     auto enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[4] = {static_cast<cuuint64_t>(W) * 8, static_cast<cuuint64_t>(C / 8), static_cast<cuuint64_t>(H),
                           static_cast<cuuint64_t>(N)};
     cuuint64_t strides[3] = {static_cast<cuuint64_t>(W) * 16, static_cast<cuuint64_t>(W) * C * 2,
                              static_cast<cuuint64_t>(H) * W * C * 2};
-    cuuint32_t box[4] = {TMA_PX * 8, 1, 1, 1};
+    cuuint32_t box[4] = {static_cast<cuuint32_t>(box_px) * 8, 1, 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(X), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -498,12 +503,12 @@ bool conv(cudaStream_t s, int *status, int N, int H, int W, const bf16 *X, const
         const int by_regs = 65536 / (regs_warp * 6);
         blocks_per_sm = std::max(1, std::min({by_smem, by_regs, 512 / ConvSmem<CI, CO>::TCOLS}));
     }
-    CUtensorMap map;
-    if (!make_xmap(&map, X, CI, N, H, W)) return false;
+    CUtensorMap map, map_tail;
+    if (!make_xmap(&map, X, CI, N, H, W, TMA_PX) || !make_xmap(&map_tail, X, CI, N, H, W, TAIL_PX)) return false;
     const int64_t ntask = static_cast<int64_t>(N) * ((W + MT - 1) / MT) * ((H + RY - 1) / RY);
     const int64_t grid = std::min<int64_t>(ntask, static_cast<int64_t>(blocks_per_sm) * sms);
-    conv3x3_kernel<CI, CO, MODE><<<static_cast<unsigned>(grid), 192, bytes, s>>>(map, Wt, bias, Y, mask, resid, N, H,
-                                                                                  W, status);
+    conv3x3_kernel<CI, CO, MODE><<<static_cast<unsigned>(grid), 192, bytes, s>>>(map, map_tail, Wt, bias, Y, mask,
+                                                                                  resid, N, H, W, status);
     return true;
 }
 
