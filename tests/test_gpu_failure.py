@@ -65,3 +65,26 @@ def test_allocation_failures_report_oom_and_context_survives():
     R.close()
     with pytest.raises(spk.SpkError):
         spk.spk_debug_fail_allocations(-1)
+
+
+def test_c_abi_from_plain_c(tmp_path):
+    """A plain C program (tests/c/abi_demo.c) linked against libspk.so reconstructs a
+    constant-interval stream through host buffers (and the asynchronous variant) and checks
+    every frame and a few error codes."""
+    import os
+    import subprocess
+
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_11639_gb300 as pkg
+    from conftest import ROOT
+    lib = pkg.build()
+    libdir = os.path.dirname(lib)
+    exe = str(tmp_path / "abi_demo")
+    subprocess.check_call(["gcc", "-O2", "-std=c11", os.path.join(ROOT, "tests", "c", "abi_demo.c"),
+                           "-I", os.path.join(ROOT, "include"), os.path.join(libdir, "libspk.so"),
+                           f"-Wl,-rpath,{libdir}", "-lm", "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert "abi_demo ok" in out.stdout
