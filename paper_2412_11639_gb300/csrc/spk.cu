@@ -552,9 +552,11 @@ __global__ void __launch_bounds__(NTHREADS, 3)
                 if constexpr (SEGMENTS) sc.release(ss);
                 else sc.release(fs);
             }
-            // rows go out every FLUSH_WORDS words: fewer warp reductions of the flush
+            // rows go out every FW words: fewer warp reductions of the flush (TFI cuts at every
+            // spike and would overflow the record ring between sparse flushes: every word)
+            constexpr int FW = ORDER == 3 ? 1 : FLUSH_WORDS;
             if constexpr (!SEGMENTS)
-                if (((j * WPT + h) % FLUSH_WORDS) == FLUSH_WORDS - 1 || (j == job.ntiles - 1 && h == WPT - 1))
+                if (((j * WPT + h) % FW) == FW - 1 || (j == job.ntiles - 1 && h == WPT - 1))
                     flush_rows(fs, sc.frontier(), valid, false);
         }
     }
