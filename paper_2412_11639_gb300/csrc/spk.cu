@@ -291,6 +291,20 @@ struct FrameSink {
         ri[s] = i;
         ++tail;
     }
+    // Room for one more record (a spike's put): the oldest goes out if the ring is full.
+    __device__ __forceinline__ void reserve() {
+        if (tail - head == QCAP) drain_one();
+    }
+    // A spike's outcome, after reserve(): the slot at tail is free, so the record is
+    // stored under a predicate and tail advances by emit -- no branch in the spike loop.
+    __device__ __forceinline__ void put(bool emit, int t, int i) {
+        const int s = slot(tail);
+        if (emit) {
+            rt[s] = t;
+            ri[s] = i;
+        }
+        tail += emit ? 1 : 0;
+    }
 };
 
 // Verification sink: the spans themselves, in time order (a one-candidate hold restores
@@ -327,6 +341,9 @@ struct SegSink {
             ht = t;
             hi = i;
         }
+    }
+    __device__ __forceinline__ void put(bool e, int t, int i) {
+        if (e) cand(t, i);
     }
     __device__ __forceinline__ void done() {
         if (held) emit(ht, hi);
@@ -516,7 +533,8 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     }
 
     bool ok = true;
-    for (int j = 0; j < job.ntiles; ++j) {
+    const int ntiles = job.ntiles, t_base = job.t_base;  // kept in registers
+    for (int j = 0; j < ntiles; ++j) {
         const int s = j % NS;
         // warp-uniform outcome: every lane leaves together if any lane's wait gave up
         if (!__all_sync(FULL, mbar_wait(&sm.full[s], (j / NS) & 1, prm.status))) {
@@ -533,7 +551,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         for (int h = 0; h < WPT; ++h) {
             uint32_t w = warp_transpose32(r[h], lane);
             if (!valid) w = 0;
-            const int base = job.t_base + j * TT + h * 32;
+            const int base = t_base + j * TT + h * 32;
             if (sc.last_t < 0 && w) {  // the stream's first spike opens the first sequence
                 const int t0 = base + __ffs(w) - 1;
                 sc.first_spike(t0);
@@ -545,8 +563,14 @@ __global__ void __launch_bounds__(NTHREADS, 3)
             while (w) {
                 const int b = __ffs(w) - 1;
                 w &= w - 1;
-                if constexpr (SEGMENTS) sc.spike(base + b, ss);
-                else sc.spike(base + b, fs);
+                if constexpr (SEGMENTS) {
+                    sc.spike(base + b, ss);
+                } else {
+                    // FSR cuts rarely: its spike keeps a branch to cand(), which makes room itself;
+                    // the tree keeps its own list
+                    if constexpr (ORDER == 2 || ORDER == 3) fs.reserve();
+                    sc.spike(base + b, fs);
+                }
             }
             if constexpr (ORDER == 5) {  // the tree's final cuts go to the sink in order
                 if constexpr (SEGMENTS) sc.release(ss);
@@ -556,7 +580,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
             // spike and would overflow the record ring between sparse flushes: every word)
             constexpr int FW = ORDER == 3 ? 1 : FLUSH_WORDS;
             if constexpr (!SEGMENTS)
-                if (((j * WPT + h) % FW) == FW - 1 || (j == job.ntiles - 1 && h == WPT - 1))
+                if (((j * WPT + h) % FW) == FW - 1 || (j == ntiles - 1 && h == WPT - 1))
                     flush_rows(fs, sc.frontier(), valid, false);
         }
     }

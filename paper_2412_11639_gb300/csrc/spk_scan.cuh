@@ -2,10 +2,14 @@
 // ORDER 3, where every interval is its own span) -- device code.
 //
 // One instance follows one pixel through time, one spike at a time.  Every cut of S_1 it
-// finds is handed to a sink as a candidate sink.cand(t_cut, i_cut): the spike time at
-// which one stable sequence ends and the next begins, and the index of the last S_1
-// element before it.  Stable sequences are the spans between consecutive cuts, starting
-// at the first spike (t0, index -1) and ending at the last spike.
+// finds is handed to a sink as a candidate (t_cut, i_cut): the spike time at which one
+// stable sequence ends and the next begins, and the index of the last S_1 element before
+// it.  An SSR (or TFI) spike hands its outcome over as sink.put(emit, t_cut, i_cut),
+// whether or not it cuts (the sink keeps the pair only if emit), so that the step has no
+// branch; the caller makes room for one record before each such spike.  FSR spikes, which
+// cut rarely, and the end of the stream call sink.cand(t_cut, i_cut) only for a cut.
+// Stable sequences are the spans between consecutive cuts, starting at the first spike
+// (t0, index -1) and ending at the last spike.
 //
 // S_1 (Def. 2, Eq. 5) is never stored: each new spike yields one interval x = t - t_prev.
 //
@@ -32,8 +36,8 @@
 //   S = min(t_latest, tq of each branch with a distance)      (frontier())
 // is final.  Sinks keep candidates sorted (one swap) and consume only final ones.
 //
-// The common step takes no data-dependent branch except the one that hands a candidate
-// to the sink, so the 32 lanes of a warp stay converged.
+// The SSR step takes no data-dependent branch, so the 32 lanes of a warp stay converged
+// and the loop body over a word's spikes is one straight-line block.
 #pragma once
 #include <stdint.h>
 
@@ -87,11 +91,13 @@ struct PixelScan {
         const int x = t - last_t;
         const int i = nint;
         if (ORDER == 3) {  // TFI (Sec. II): every interval is its own span
-            if (i > 0) sink.cand(last_t, i - 1);
+            sink.put(i > 0, last_t, i - 1);
         } else if (ORDER == 1) {
             const int lo = min(v0, x), hi = max(v1, x);
             const bool brk = hi - lo > 1;
-            if (brk) sink.cand(last_t, i - 1);  // the sequence ends at spike last_t
+            // the sequence ends at spike last_t (rare: FSR keeps the branch, which measured
+            // faster than the predicated hand-off of SSR for this lighter step)
+            if (brk) sink.cand(last_t, i - 1);
             v0 = brk ? x : lo;
             v1 = brk ? x : hi;
         } else {
@@ -108,8 +114,8 @@ struct PixelScan {
             const bool viol = (isv0 || isv1) && lo != 0 && wide;  // S_2 breaks before d
             const bool rst = lo == 0 || wide;
             const int wlo = rst ? d : nlo, whi = rst ? d : nhi;
-            if (viol || (brk && v0 > 0))  // S_2 cut after q, or FSR cut at the previous spike
-                sink.cand(viol ? tq : last_t, viol ? q : i - 1);
+            // S_2 cut after q, or FSR cut at the previous spike
+            sink.put(viol || (brk && v0 > 0), viol ? tq : last_t, viol ? q : i - 1);
             const bool u0 = isv0 || brk, u1 = isv1 || nv1;
             q0 = u0 ? i : q0;
             tq0 = u0 ? t : tq0;
