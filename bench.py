@@ -44,6 +44,9 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="dynamic_250x400x20000")
     ap.add_argument("--T", type=int, default=0,
                     help="cut the workload to its first T steps (profiling a smaller case)")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="reconstruct only the first ROWS rows of the same stream (fewer blocks "
+                         "per SM: shows whether the scan is bound per warp or per SM)")
     ap.add_argument("--order", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="method: 1 FSR, 2 SSR (default), 3 TFI, 4 TFP (window --tfp-window), "
                          "5 the n-order tree (--stability-order levels)")
@@ -174,6 +177,19 @@ def workload_stream(name: str, rank: int, world: int, device: int | None = None,
     return w, np.load(cache, mmap_mode=None)
 
 
+def cut_rows(w, st, rows: int):
+    """The first `rows` rows of every frame of a packed stream, repacked at their own pitch
+    (pixel p < rows * W keeps its bit; the bits past it in the last byte are padding)."""
+    import numpy as np
+    import spkgen
+    if not 0 < rows <= w.H:
+        raise SystemExit(f"--rows must be in 1..{w.H}")
+    n = (rows * w.W + 7) // 8
+    out = np.zeros((st.shape[0], spkgen.pitch(rows, w.W)), dtype=np.uint8)
+    out[:, :n] = st[:, :n]
+    return w.resized(H=rows, name=f"{w.name}[rows:{rows}]"), out
+
+
 def measured_peak():
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -190,8 +206,9 @@ def kernel_source_sha() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(workload: str, order: int):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+def recorded_profile(workload: str, order: int):
+    """(DRAM bytes per launch, ALU-pipe busy % of peak) from the committed ncu summary, if it
+    matches this source and workload; (None, None) otherwise."""
     try:
         kv = {}
         for line in open(TRAFFIC_FILE):
@@ -200,10 +217,11 @@ def recorded_traffic(workload: str, order: int):
                 kv[k.strip()] = v.strip()
         if (kv.get("workload") == workload and int(kv.get("order", -1)) == order
                 and kv.get("source_sha256") == kernel_source_sha()):
-            return float(kv["dram_bytes_per_launch"])
+            alu = kv.get("alu_pipe_active_pct")
+            return float(kv["dram_bytes_per_launch"]), (float(alu) if alu else None)
     except (OSError, ValueError, KeyError):
         pass
-    return None
+    return None, None
 
 
 # ------------------------------------------------------------------ CPU oracle ----
@@ -287,6 +305,8 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     w, st = workload_stream(args.workload, rank, world, device=local_rank, T_cut=args.T)
+    if args.rows:
+        w, st = cut_rows(w, st, args.rows)
     dtype = torch.float16 if w.out_dtype == "f16" else torch.float32
     esz = 2 if dtype == torch.float16 else 4
     R = pkg.Reconstructor(order=args.order, stride=w.stride, dtype=dtype, device=local_rank,
@@ -383,7 +403,7 @@ def run_ours(args, rank, world, local_rank):
         oracle.set_threads(0)
         cpu["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
                               "sample": f"{n1} pixels x {w.T_out} frames, {dt1:.1f} s"}
-    traffic = recorded_traffic(w.name, args.order)
+    traffic, alu_pct = recorded_profile(w.name, args.order)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "input_Gpixel_steps_per_s": w.P * w.T * K * world / (total_ms / 1e3) / 1e9,
@@ -394,7 +414,10 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "kernel": "spk_tfp_kernel" if args.order == 4 else KERNEL, "kernel_ms": kern_ms,
-                     "algorithmic_bytes_per_launch": alg_bytes},
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     # what bounds the scan: its integer compare/select work keeps the SM's ALU
+                     # pipe busy (ncu, same source); null once the kernel has changed
+                     "alu_pipe_busy_pct_of_peak": alu_pct},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
