@@ -80,7 +80,7 @@ struct PixelScan {
         int S = last_t;
         if (ORDER >= 2) {
             if (dlo0 != 0) S = min(S, tq0);
-            if (dlo1 != 0) S = min(S, tq1);
+            if (dlo1 != 0 && v1 != 0) S = min(S, tq1);  // branch 1 exists only with v1
         }
         return S;
     }
@@ -116,15 +116,18 @@ struct PixelScan {
             const int wlo = rst ? d : nlo, whi = rst ? d : nhi;
             // S_2 cut after q, or FSR cut at the previous spike
             sink.put(viol || (brk && v0 > 0), viol ? tq : last_t, viol ? q : i - 1);
+            // the branch this element belongs to takes (i, t, range); an opening element (FSR
+            // break: branch 0; the other value's first occurrence: branch 1) has no distance
             const bool u0 = isv0 || brk, u1 = isv1 || nv1;
+            const int nlo0 = (brk || nv1) ? 0 : wlo;
             q0 = u0 ? i : q0;
             tq0 = u0 ? t : tq0;
-            dlo0 = brk ? 0 : (isv0 ? wlo : dlo0);
-            dhi0 = isv0 ? whi : dhi0;
+            dlo0 = u0 ? nlo0 : dlo0;
+            dhi0 = u0 ? whi : dhi0;
             q1 = u1 ? i : q1;
             tq1 = u1 ? t : tq1;
-            dlo1 = (brk || nv1) ? 0 : (isv1 ? wlo : dlo1);
-            dhi1 = isv1 ? whi : dhi1;
+            dlo1 = u1 ? nlo0 : dlo1;  // (left as is by an FSR break: unused until v1 is set)
+            dhi1 = u1 ? whi : dhi1;
             v1 = nv1 ? x : (brk ? 0 : v1);
             v0 = brk ? x : v0;
         }
