@@ -31,8 +31,8 @@
 // time order, but by one place at most: a branch can run ahead of the other only through
 // a distance of 1, which breaks its S_2 at most once before the other branch's next
 // occurrence.  A candidate is final once no earlier cut can still appear; later cuts of a
-// branch fall at or after its tq (if it has a distance) and FSR cuts at or after the
-// latest spike, so every cut at or before
+// branch fall at or after its tq (if it has a distance; branch 1 only while the second
+// value is set) and FSR cuts at or after the latest spike, so every cut at or before
 //   S = min(t_latest, tq of each branch with a distance)      (frontier())
 // is final.  Sinks keep candidates sorted (one swap) and consume only final ones.
 //
@@ -45,9 +45,14 @@
 #define SPK_DEV __device__ __forceinline__
 #else
 #define SPK_DEV inline
+#include <algorithm>
 #endif
 
 namespace spk {
+#if !defined(__CUDACC__)
+using std::max;  // host builds of this header (the scan's CPU check in tests/c)
+using std::min;
+#endif
 
 constexpr int NO_VALUE = -100;  // v0 before the first interval: never equals an interval
 

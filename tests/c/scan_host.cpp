@@ -1,0 +1,110 @@
+// Host build of the kernel's own per-pixel scan (paper_2412_11639_gb300/csrc/spk_scan.cuh),
+// driven word by word exactly as the CUDA kernel drives it: the first spike opens the
+// stream, an all-ones word may be absorbed whole, every other spike goes through spike().
+// It writes each pixel's stable sequences so that a test can compare them with the oracle
+// on the CPU, and it checks the two properties the kernel's record ring relies on:
+//   * a candidate arrives at most one place before its predecessor (the ring's single swap
+//     restores time order), and
+//   * no candidate arrives before a frontier() reported after an earlier word, and no two
+//     cuts share a time (so a record at or before the frontier is final).
+//
+// usage: scan_host <stream.bin> <P> <T> <pitch> <order 1|2> <out.bin>
+// stream.bin: uint8 [T][pitch], pixel p is bit p % 8 of byte p / 8 (the library's layout).
+// out.bin: int32 counts[P], then for every pixel in order its sequences as int32 triples
+// (t_start, t_end, n_intervals).  Exit status 0, or 3 if a property above failed.
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "../../paper_2412_11639_gb300/csrc/spk_scan.cuh"
+
+namespace {
+
+struct Cuts {
+    std::vector<int> t, i;
+    void cand(int tc, int ic) {
+        t.push_back(tc);
+        i.push_back(ic);
+    }
+    void put(bool emit, int tc, int ic) {
+        if (emit) cand(tc, ic);
+    }
+};
+
+template <int ORDER>
+int run(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, FILE *out) {
+    std::vector<int32_t> counts(P, 0), spans;
+    int bad = 0;
+    for (int64_t p = 0; p < P; ++p) {
+        spk::PixelScan<ORDER> sc;
+        sc.init();
+        Cuts c;
+        int t0 = -1, frontier = -1;  // latest frontier reported after a word
+        size_t checked = 0;          // candidates already checked against a frontier
+        for (int base = 0; base < T; base += 32) {
+            uint32_t w = 0;
+            for (int k = 0; k < 32 && base + k < T; ++k)
+                w |= static_cast<uint32_t>((s[(base + k) * pitch + p / 8] >> (p % 8)) & 1) << k;
+            if (sc.last_t < 0 && w) {
+                t0 = base + __builtin_ctz(w);
+                sc.first_spike(t0);
+                w &= w - 1;
+            }
+            if (w == 0xffffffffu && sc.absorb_ones(base)) w = 0;
+            while (w) {
+                const int b = __builtin_ctz(w);
+                w &= w - 1;
+                sc.spike(base + b, c);
+            }
+            for (; checked < c.t.size(); ++checked)
+                if (c.t[checked] < frontier) bad |= 2;
+            if (sc.last_t >= 0) frontier = sc.frontier();
+        }
+        sc.finish(c);
+        for (; checked < c.t.size(); ++checked)
+            if (c.t[checked] < frontier) bad |= 2;
+        // one adjacent swap per candidate, as the record ring does, then strictly increasing
+        for (size_t j = 1; j < c.t.size(); ++j)
+            if (c.t[j] < c.t[j - 1]) {
+                std::swap(c.t[j], c.t[j - 1]);
+                std::swap(c.i[j], c.i[j - 1]);
+                if (j >= 2 && c.t[j - 1] <= c.t[j - 2]) bad |= 1;
+            }
+        for (size_t j = 1; j < c.t.size(); ++j)
+            if (c.t[j] <= c.t[j - 1]) bad |= 1;
+        int ct = t0, ci = -1;
+        for (size_t j = 0; j < c.t.size(); ++j) {
+            spans.push_back(ct);
+            spans.push_back(c.t[j]);
+            spans.push_back(c.i[j] - ci);
+            ct = c.t[j];
+            ci = c.i[j];
+        }
+        counts[p] = static_cast<int32_t>(c.t.size());
+    }
+    fwrite(counts.data(), sizeof(int32_t), counts.size(), out);
+    fwrite(spans.data(), sizeof(int32_t), spans.size(), out);
+    return bad;
+}
+
+}  // namespace
+
+int main(int argc, char **argv) {
+    if (argc != 7) {
+        fprintf(stderr, "usage: scan_host stream.bin P T pitch order out.bin\n");
+        return 2;
+    }
+    const int64_t P = atoll(argv[2]), pitch = atoll(argv[4]);
+    const int T = atoi(argv[3]), order = atoi(argv[5]);
+    std::vector<uint8_t> s(static_cast<size_t>(pitch) * T);
+    FILE *f = fopen(argv[1], "rb");
+    if (!f || fread(s.data(), 1, s.size(), f) != s.size()) return 2;
+    fclose(f);
+    FILE *out = fopen(argv[6], "wb");
+    if (!out) return 2;
+    const int bad = order == 1 ? run<1>(s, P, T, pitch, out) : run<2>(s, P, T, pitch, out);
+    fclose(out);
+    if (bad) fprintf(stderr, "property failed: %s%s\n", bad & 1 ? "order " : "", bad & 2 ? "frontier" : "");
+    return bad ? 3 : 0;
+}

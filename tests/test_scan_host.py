@@ -1,0 +1,88 @@
+"""The kernel's own per-pixel scan (csrc/spk_scan.cuh), compiled for the host, against the
+fp64 oracle -- on the CPU, no GPU needed.
+
+tests/c/scan_host.cpp drives PixelScan word by word as the CUDA kernel does (first spike,
+whole-word absorption of steady ones, one spike() per remaining spike) and writes every
+pixel's stable sequences.  They must equal the oracle's (Def. 2 greedy FSR, the two S_2
+branches of SSR; Sec. III-B) exactly: spike times of every cut and interval counts.  The
+program also checks the orderings the kernel's record ring depends on (a candidate at most
+one place early, cut times unique, nothing before a reported frontier) and exits 3 if one
+fails.
+This pins the scan state machine itself; the GPU tests pin the kernel around it.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import spkgen
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def scan_host(tmp_path_factory):
+    exe = str(tmp_path_factory.mktemp("scan_host") / "scan_host")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", os.path.join(ROOT, "tests", "c", "scan_host.cpp"),
+                           "-o", exe])
+    return exe
+
+
+def run_host(exe, tmp_path, st, P, T, order):
+    st = np.ascontiguousarray(st, dtype=np.uint8)
+    src, dst = tmp_path / "stream.bin", tmp_path / "spans.bin"
+    st.tofile(src)
+    r = subprocess.run([exe, str(src), str(P), str(T), str(st.shape[1]), str(order), str(dst)],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    raw = np.fromfile(dst, dtype=np.int32)
+    counts = raw[:P]
+    spans = raw[P:].reshape(-1, 3)
+    assert spans.shape[0] == counts.sum()
+    return counts, spans
+
+
+def check_against_oracle(exe, tmp_path, st, H, W, T, order):
+    P = H * W
+    counts, spans = run_host(exe, tmp_path, st, P, T, order)
+    ref = oracle.reconstruct(st, H, W, T, 1.0, order, 1, frames=False, segments=True)
+    assert np.array_equal(counts, ref.nseg), "sequence counts differ"
+    assert np.array_equal(spans[:, 0], ref.seg_ts), "sequence starts differ"
+    assert np.array_equal(spans[:, 1], ref.seg_te), "sequence ends differ"
+    assert np.array_equal(spans[:, 2], ref.seg_n), "interval counts differ"
+    return counts
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("recipe,H,W,T", [
+    ("dynamic_250x400x20000", 20, 50, 3000),   # moving scene, step events, dark noise
+    ("large_1000x1000x20000", 16, 40, 2500),   # moving scene down to I = 0.005
+    ("static_250x400x2000", 16, 40, 2000),     # constant intensity per pixel (Theorem 1)
+])
+def test_scan_equals_oracle_on_scenes(scan_host, tmp_path, recipe, H, W, T, order):
+    w = spkgen.WORKLOADS[recipe].resized(H=H, W=W, T=T)
+    st, _ = spkgen.make_stream(w)
+    counts = check_against_oracle(scan_host, tmp_path, st, H, W, T, order)
+    if w.moving:
+        assert counts.sum() > 10 * H * W  # cuts were exercised
+    else:
+        assert counts.max() == 1  # constant intensity: one stable sequence (Theorem 1)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("density", [0.1, 0.5, 0.9, 0.97])
+def test_scan_equals_oracle_on_random_bits(scan_host, tmp_path, density, order):
+    H, W, T = 10, 40, 1500  # T not a multiple of 32: a ragged last word
+    bits = spkgen.random_bits(T, H * W, density, seed=int(density * 1000) + order)
+    st = spkgen.pack(bits, H, W)
+    check_against_oracle(scan_host, tmp_path, st, H, W, T, order)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_scan_equals_oracle_on_every_16_step_pattern(scan_host, tmp_path, order):
+    T, P = 16, 1 << 16
+    p = np.arange(P, dtype=np.int64)
+    bits = np.stack([((p >> t) & 1).astype(np.uint8) for t in range(T)])  # [T][P]
+    st = spkgen.pack(bits, 256, 256)
+    check_against_oracle(scan_host, tmp_path, st, 256, 256, T, order)
