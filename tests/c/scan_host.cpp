@@ -8,7 +8,8 @@
 //   * no candidate arrives before a frontier() reported after an earlier word, and no two
 //     cuts share a time (so a record at or before the frontier is final).
 //
-// usage: scan_host <stream.bin> <P> <T> <pitch> <order 1|2> <out.bin>
+// usage: scan_host <stream.bin> <P> <T> <pitch> <order 1..5> <out.bin>
+// (1 FSR, 2 SSR: PixelScan; 3..5: the general n-order tree TreeScan of the same header)
 // stream.bin: uint8 [T][pitch], pixel p is bit p % 8 of byte p / 8 (the library's layout).
 // out.bin: int32 counts[P], then for every pixel in order its sequences as int32 triples
 // (t_start, t_end, n_intervals).  Exit status 0, or 3 if a property above failed.
@@ -88,6 +89,54 @@ int run(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, FILE *ou
     return bad;
 }
 
+// The general n-order tree (orders 3..5), driven as the kernel drives it: after every word
+// the final pending cuts go to the sink in time order (release); they must arrive strictly
+// increasing and the tree's own overflow flag must stay clear.
+int run_tree(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, int n, FILE *out) {
+    std::vector<int32_t> counts(P, 0), spans;
+    int bad = 0;
+    auto *sc = new spk::TreeScan;  // about 1.4 KB of node arrays
+    for (int64_t p = 0; p < P; ++p) {
+        sc->init(n);
+        Cuts c;
+        int t0 = -1;
+        for (int base = 0; base < T; base += 32) {
+            uint32_t w = 0;
+            for (int k = 0; k < 32 && base + k < T; ++k)
+                w |= static_cast<uint32_t>((s[(base + k) * pitch + p / 8] >> (p % 8)) & 1) << k;
+            if (sc->last_t < 0 && w) {
+                t0 = base + __builtin_ctz(w);
+                sc->first_spike(t0);
+                w &= w - 1;
+            }
+            if (w == 0xffffffffu && sc->absorb_ones(base)) w = 0;
+            while (w) {
+                const int b = __builtin_ctz(w);
+                w &= w - 1;
+                sc->spike(base + b, c);
+            }
+            sc->release(c);
+        }
+        sc->finish(c);
+        if (sc->bad) bad |= 4;
+        for (size_t j = 1; j < c.t.size(); ++j)
+            if (c.t[j] <= c.t[j - 1]) bad |= 1;
+        int ct = t0, ci = -1;
+        for (size_t j = 0; j < c.t.size(); ++j) {
+            spans.push_back(ct);
+            spans.push_back(c.t[j]);
+            spans.push_back(c.i[j] - ci);
+            ct = c.t[j];
+            ci = c.i[j];
+        }
+        counts[p] = static_cast<int32_t>(c.t.size());
+    }
+    delete sc;
+    fwrite(counts.data(), sizeof(int32_t), counts.size(), out);
+    fwrite(spans.data(), sizeof(int32_t), spans.size(), out);
+    return bad;
+}
+
 }  // namespace
 
 int main(int argc, char **argv) {
@@ -103,8 +152,13 @@ int main(int argc, char **argv) {
     fclose(f);
     FILE *out = fopen(argv[6], "wb");
     if (!out) return 2;
-    const int bad = order == 1 ? run<1>(s, P, T, pitch, out) : run<2>(s, P, T, pitch, out);
+    if (order < 1 || order > spk::TREE_MAX) return 2;
+    const int bad = order == 1   ? run<1>(s, P, T, pitch, out)
+                    : order == 2 ? run<2>(s, P, T, pitch, out)
+                                 : run_tree(s, P, T, pitch, order, out);
     fclose(out);
-    if (bad) fprintf(stderr, "property failed: %s%s\n", bad & 1 ? "order " : "", bad & 2 ? "frontier" : "");
+    if (bad)
+        fprintf(stderr, "property failed: %s%s%s\n", bad & 1 ? "order " : "", bad & 2 ? "frontier " : "",
+                bad & 4 ? "tree pending list" : "");
     return bad ? 3 : 0;
 }

@@ -1,5 +1,5 @@
 """The kernel's own per-pixel scan (csrc/spk_scan.cuh), compiled for the host, against the
-fp64 oracle -- on the CPU, no GPU needed.
+fp64 oracle -- on the CPU, no GPU needed (FSR, SSR, and the n-order tree of orders 3..5).
 
 tests/c/scan_host.cpp drives PixelScan word by word as the CUDA kernel does (first spike,
 whole-word absorption of steady ones, one spike() per remaining spike) and writes every
@@ -86,3 +86,25 @@ def test_scan_equals_oracle_on_every_16_step_pattern(scan_host, tmp_path, order)
     bits = np.stack([((p >> t) & 1).astype(np.uint8) for t in range(T)])  # [T][P]
     st = spkgen.pack(bits, 256, 256)
     check_against_oracle(scan_host, tmp_path, st, 256, 256, T, order)
+
+
+@pytest.mark.parametrize("order", [3, 4, 5])
+@pytest.mark.parametrize("recipe,H,W,T", [
+    ("dynamic_250x400x20000", 12, 40, 2500),
+    ("large_1000x1000x20000", 10, 40, 2000),
+])
+def test_tree_equals_oracle_on_scenes(scan_host, tmp_path, recipe, H, W, T, order):
+    """The n-order tree (Fig. 1 caption, Sec. III-B) of the same header, orders 3..5."""
+    w = spkgen.WORKLOADS[recipe].resized(H=H, W=W, T=T)
+    st, _ = spkgen.make_stream(w)
+    counts = check_against_oracle(scan_host, tmp_path, st, H, W, T, order)
+    assert counts.sum() > 10 * H * W
+
+
+@pytest.mark.parametrize("order", [3, 5])
+@pytest.mark.parametrize("density", [0.3, 0.7, 0.95])
+def test_tree_equals_oracle_on_random_bits(scan_host, tmp_path, density, order):
+    H, W, T = 8, 40, 1200
+    bits = spkgen.random_bits(T, H * W, density, seed=int(density * 1000) + 10 * order)
+    st = spkgen.pack(bits, H, W)
+    check_against_oracle(scan_host, tmp_path, st, H, W, T, order)
