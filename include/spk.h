@@ -79,9 +79,13 @@ typedef struct spk_config {
 
 typedef struct spk_ctx spk_ctx;
 
-/* Creates a context on cfg->device.  Allocates a small device status word; scratch
- * buffers are allocated lazily by the calls that need them.  *out receives the handle
- * (NULL on failure).  Errors: SPK_ERR_ARG (bad cfg), SPK_ERR_CUDA, SPK_ERR_OOM. */
+/* Creates a context on cfg->device for one reconstruction method of the paper's problem
+ * statement (Sec. II: a spike stream S_0 in, intensity images out; FSR and SSR of
+ * Sec. III-B, the TFI and TFP baselines of Sec. II).  cfg fixes the method, the frame
+ * stride and output type, the device and the CUDA stream every later call launches on.
+ * Allocates a 16-byte device status word; scratch buffers are allocated lazily by the
+ * calls that need them.  *out receives the handle (NULL on failure); spk_destroy frees it.
+ * Errors: SPK_ERR_ARG (bad cfg), SPK_ERR_CUDA (no device), SPK_ERR_OOM. */
 int spk_create(spk_ctx **out, const spk_config *cfg);
 
 /* Frees every buffer owned by ctx.  NULL is a no-op returning SPK_OK. */
@@ -181,16 +185,20 @@ int spk_get_tile(const spk_ctx *ctx);
  * SPK_ERR_ARG for stream jobs. */
 int spk_autotune(spk_ctx *ctx, const spk_job *jobs, int njobs, int *best_tile);
 
-/* Verification export: the stable sequences themselves (the records the paper's FPGA
- * encoder emits, Sec. III-C).  For pixel p, counts[p] receives the number of sequences;
- * sequence j < cap is written at index j*H*W + p of t_start (spike time opening it),
- * t_end (spike time closing it), n_int (number of intervals N) and value
- * (threshold * N / (t_end - t_start), fp32).  cap may be 0 (counts only; the four
- * arrays may then be NULL).  All pointers are device memory.  Asynchronous.
- * Errors: SPK_ERR_ARG, SPK_ERR_CUDA. */
+/* Verification export: per pixel the spike count K and the stable sequences themselves
+ * (the records the paper's FPGA encoder emits, Sec. III-C).  For pixel p:
+ *   spike_counts[p]  K, the number of spikes of the pixel in the T steps: S_1 (Def. 2,
+ *                    Eq. 5) has K - 1 intervals, so K < 2 leaves no sequence.  May be NULL.
+ *   counts[p]        the number of stable sequences;
+ *   sequence j < cap is written at index j*H*W + p of t_start (spike time opening it),
+ *   t_end (spike time closing it), n_int (number of intervals N) and value
+ *   (threshold * N / (t_end - t_start), fp32, Eq. 4).
+ * cap may be 0 (counts only; the four sequence arrays may then be NULL).  All pointers
+ * are int32 / fp32 device memory owned by the caller.  SPK_TFP has no sequences and is
+ * rejected.  Asynchronous.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA. */
 int spk_segments(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold,
-                 int32_t *counts, int32_t *t_start, int32_t *t_end, int32_t *n_int,
-                 float *value, int cap);
+                 int32_t *spike_counts, int32_t *counts, int32_t *t_start, int32_t *t_end,
+                 int32_t *n_int, float *value, int cap);
 
 /* Waits for the context's stream, then reads and clears the device status word:
  * SPK_ERR_TIMEOUT if a bounded device wait gave up, SPK_ERR_INTERNAL if a consistency

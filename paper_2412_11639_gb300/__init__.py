@@ -65,20 +65,23 @@ class Reconstructor:
         spk_reconstruct(self.ctx, stream, H, W, T, threshold, out)
         return out
 
-    def segments(self, stream, H: int, W: int, T: int, threshold: float = 1.0, cap=None):
-        """Stable sequences per pixel: (counts [P], t_start, t_end, n, value [cap][P])."""
+    def segments(self, stream, H: int, W: int, T: int, threshold: float = 1.0, cap=None,
+                 spikes: bool = False):
+        """Stable sequences per pixel: (counts [P], t_start, t_end, n, value [cap][P]);
+        with spikes=True the spike counts K [P] come first."""
         torch = self.torch
         P = H * W
         dev = f"cuda:{self.device}"
         counts = torch.empty(P, dtype=torch.int32, device=dev)
+        K = torch.empty(P, dtype=torch.int32, device=dev) if spikes else None
         if cap is None:
-            spk_segments(self.ctx, stream, H, W, T, threshold, counts, None, None, None, None, 0)
+            spk_segments(self.ctx, stream, H, W, T, threshold, None, counts, None, None, None, None, 0)
             self.synchronize()
             cap = int(counts.max().item()) if P else 0
         arrs = [torch.empty((max(cap, 1), P), dtype=d, device=dev)
                 for d in (torch.int32, torch.int32, torch.int32, torch.float32)]
-        spk_segments(self.ctx, stream, H, W, T, threshold, counts, *arrs, cap)
-        return (counts, *arrs)
+        spk_segments(self.ctx, stream, H, W, T, threshold, K, counts, *arrs, cap)
+        return (K, counts, *arrs) if spikes else (counts, *arrs)
 
     def synchronize(self):
         spk_synchronize(self.ctx)

@@ -99,7 +99,8 @@ struct Batch {
     Job jobs[MAXJ];
     int njobs;
     int *status;
-    int32_t *counts, *seg_ts, *seg_te, *seg_n;  // segments mode (one job)
+    int32_t *spikes;                            // segments mode (one job): K per pixel, or nullptr
+    int32_t *counts, *seg_ts, *seg_te, *seg_n;  // segments mode: the stable sequences
     float *seg_v;
     int cap;
 };
@@ -592,6 +593,8 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         sc.finish(ss);
         ss.done();
         if (valid) prm.counts[p] = ss.cnt;
+        // K, the number of spikes (S_1 has K - 1 elements, Def. 2): the scan's own count
+        if (valid && prm.spikes) prm.spikes[p] = sc.last_t >= 0 ? sc.nint + 1 : 0;
         if constexpr (ORDER == 5)
             if (valid && sc.bad) atomicOr(prm.status, DEV_INTERNAL);
     } else if (job.flags & JOB_LAST) {
@@ -1064,7 +1067,8 @@ int fill_job(spk_ctx *ctx, CUtensorMap *map, Job *job, const uint8_t *stream, in
 }
 
 int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold, void *out,
-             int32_t *counts, int32_t *ts, int32_t *te, int32_t *n, float *v, int cap, bool segments) {
+             int32_t *spikes, int32_t *counts, int32_t *ts, int32_t *te, int32_t *n, float *v, int cap,
+             bool segments) {
     if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
     Batch<1> prm{};
     const int tile = tile_of(ctx, segments);
@@ -1073,6 +1077,7 @@ int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float thr
     if (nb < 0) return nb;
     prm.njobs = 1;
     prm.status = ctx->d_status;
+    prm.spikes = spikes;
     prm.counts = counts;
     prm.seg_ts = ts;
     prm.seg_te = te;
@@ -1169,22 +1174,24 @@ int spk_reconstruct(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, fl
     if (overlaps(stream, in_bytes, out_frames, out_bytes)) return fail(ctx, SPK_ERR_ARG, "out_frames overlaps stream");
     if (!is_device_ptr(stream) || !is_device_ptr(out_frames))
         return fail(ctx, SPK_ERR_ARG, "stream and out_frames must be device memory");
-    return run_scan(ctx, stream, H, W, T, threshold, out_frames, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+    return run_scan(ctx, stream, H, W, T, threshold, out_frames, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
                     false);
 }
 
-int spk_segments(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold, int32_t *counts,
-                 int32_t *t_start, int32_t *t_end, int32_t *n_int, float *value, int cap) {
+int spk_segments(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold, int32_t *spike_counts,
+                 int32_t *counts, int32_t *t_start, int32_t *t_end, int32_t *n_int, float *value, int cap) {
     int rc = check_stream_args(ctx, stream, H, W, T, threshold);
     if (rc) return rc;
     ctx->msg[0] = 0;
     if (ctx->cfg.method == SPK_TFP) return fail(ctx, SPK_ERR_ARG, "TFP has no stable spans");
     if (!counts || cap < 0) return fail(ctx, SPK_ERR_ARG, "counts is NULL or cap < 0");
     if (cap > 0 && (!t_start || !t_end || !n_int || !value)) return fail(ctx, SPK_ERR_ARG, "segment arrays are NULL");
-    if (!is_device_ptr(stream) || !is_device_ptr(counts)) return fail(ctx, SPK_ERR_ARG, "pointers must be device memory");
+    if (!is_device_ptr(stream) || !is_device_ptr(counts) || (spike_counts && !is_device_ptr(spike_counts)))
+        return fail(ctx, SPK_ERR_ARG, "pointers must be device memory");
     if (cap > 0 && (!is_device_ptr(t_start) || !is_device_ptr(t_end) || !is_device_ptr(n_int) || !is_device_ptr(value)))
         return fail(ctx, SPK_ERR_ARG, "pointers must be device memory");
-    return run_scan(ctx, stream, H, W, T, threshold, nullptr, counts, t_start, t_end, n_int, value, cap, true);
+    return run_scan(ctx, stream, H, W, T, threshold, nullptr, spike_counts, counts, t_start, t_end, n_int, value, cap,
+                    true);
 }
 
 int spk_synchronize(spk_ctx *ctx) {
@@ -1461,8 +1468,8 @@ int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W,
     }
     if (cudaMemcpyAsync(ctx->d_in, host_stream, in_bytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
         return fail(ctx, SPK_ERR_CUDA, "H2D copy: %s", cudaGetErrorString(cudaGetLastError()));
-    rc = run_scan(ctx, ctx->d_in, H, W, T, threshold, ctx->d_out, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
-                  false);
+    rc = run_scan(ctx, ctx->d_in, H, W, T, threshold, ctx->d_out, nullptr, nullptr, nullptr, nullptr, nullptr,
+                  nullptr, 0, false);
     if (rc) return rc;
     if (cudaMemcpyAsync(host_frames, ctx->d_out, out_bytes, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
         return fail(ctx, SPK_ERR_CUDA, "D2H copy: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1522,7 +1529,7 @@ int spk_reconstruct_host_async(spk_ctx *ctx, const uint8_t *host_stream, int H, 
     cudaStream_t own = ctx->stream;  // the scan launches on the lane
     ctx->stream = ls;
     rc = run_scan(ctx, ctx->lane_in[l], H, W, T, threshold, ctx->lane_out[l], nullptr, nullptr, nullptr, nullptr,
-                  nullptr, 0, false);
+                  nullptr, nullptr, 0, false);
     ctx->stream = own;
     if (rc) return rc;
     if (cudaMemcpyAsync(host_frames, ctx->lane_out[l], out_bytes, cudaMemcpyDeviceToHost, ls) != cudaSuccess)
@@ -1604,7 +1611,11 @@ extern "C" int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t
     tmp.tile = TT_DEFAULT;
     tmp.stream = static_cast<cudaStream_t>(cfg->stream);
     tmp.d_status = d_status;
+    // A failure after the first enqueue waits for what was enqueued, so that no copy still
+    // reads host_stream (or writes the array) once the call has returned.
     auto bail = [&](int code) {
+        cudaStreamSynchronize(tmp.stream);
+        cudaGetLastError();
         snprintf(g_create_msg, sizeof(g_create_msg), "%.480s", tmp.msg);
         return code;
     };
@@ -1614,7 +1625,8 @@ extern "C" int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t
         fail(&tmp, SPK_ERR_CUDA, "H2D staging: %s", cudaGetErrorString(cudaGetLastError()));
         return bail(SPK_ERR_CUDA);
     }
-    int rc = run_scan(&tmp, d_in, H, W, T, threshold, d_out, nullptr, nullptr, nullptr, nullptr, nullptr, 0, false);
+    int rc = run_scan(&tmp, d_in, H, W, T, threshold, d_out, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                      false);
     if (rc) return bail(rc);
     if (cudaMemcpyAsync(host_frames, d_out, out_bytes, cudaMemcpyDeviceToHost, tmp.stream) != cudaSuccess) {
         fail(&tmp, SPK_ERR_CUDA, "D2H copy: %s", cudaGetErrorString(cudaGetLastError()));

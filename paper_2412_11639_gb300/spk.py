@@ -72,7 +72,7 @@ def load(path: str | None = None):
     lib.spk_reconstruct_host.restype = i32
     lib.spk_reconstruct_host_async.argtypes = [vp, vp, i32, i32, i32, f32, vp]
     lib.spk_reconstruct_host_async.restype = i32
-    lib.spk_segments.argtypes = [vp, vp, i32, i32, i32, f32, vp, vp, vp, vp, vp, i32]
+    lib.spk_segments.argtypes = [vp, vp, i32, i32, i32, f32, vp, vp, vp, vp, vp, vp, i32]
     lib.spk_segments.restype = i32
     lib.spk_synchronize.argtypes = [vp]
     lib.spk_synchronize.restype = i32
@@ -146,6 +146,9 @@ def _check(ctx, rc):
     return rc
 
 
+_CTX_FRAMES = {}  # context handle -> (frame_stride, bytes per output value), for host-buffer checks
+
+
 def spk_create(method: int = SPK_SSR, frame_stride: int = 1, out_dtype: int = SPK_F32, device: int = 0,
                stream: int | None = None, tfp_window: int = 32, stability_order: int = 3):
     lib = load()
@@ -153,11 +156,43 @@ def spk_create(method: int = SPK_SSR, frame_stride: int = 1, out_dtype: int = SP
     ctx = _c.c_void_p()
     rc = lib.spk_create(_c.byref(ctx), _c.byref(cfg))
     _check(None, rc)
+    _CTX_FRAMES[ctx.value] = (frame_stride, 2 if out_dtype == SPK_F16 else 4)
     return ctx
 
 
 def spk_destroy(ctx):
+    _CTX_FRAMES.pop(getattr(ctx, "value", ctx), None)
     return load().spk_destroy(ctx)
+
+
+def _nbytes_contiguous(x, name):
+    """Size in bytes of a C-contiguous host buffer (numpy array or CPU tensor)."""
+    if hasattr(x, "is_contiguous"):          # torch tensor
+        if x.is_cuda or not x.is_contiguous():
+            raise ValueError(f"{name} must be a C-contiguous host tensor")
+        return x.numel() * x.element_size()
+    flags = getattr(x, "flags", None)
+    if flags is None or not flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name} must be a C-contiguous array")
+    return x.nbytes
+
+
+def _check_host_buffers(host_stream, host_frames, H, W, T, stride, esz, frames_dtype=None):
+    """The C side reads T * pitch bytes and writes T_out * H * W * esz bytes: refuse buffers
+    that are smaller, strided, or (when known) of the wrong element size."""
+    if H <= 0 or W <= 0 or T <= 0 or stride <= 0:
+        return  # the library rejects these itself
+    need_in = T * ((((H * W + 7) // 8) + 15) // 16 * 16)
+    need_out = -(-T // stride) * H * W * esz
+    if _nbytes_contiguous(host_stream, "host_stream") < need_in:
+        raise ValueError(f"host_stream holds fewer than T * pitch = {need_in} bytes")
+    if _nbytes_contiguous(host_frames, "host_frames") < need_out:
+        raise ValueError(f"host_frames holds fewer than T_out * H * W * {esz} = {need_out} bytes")
+    item = getattr(getattr(host_frames, "dtype", None), "itemsize", None)
+    if item is None and hasattr(host_frames, "element_size"):
+        item = host_frames.element_size()
+    if item is not None and item != esz:
+        raise ValueError(f"host_frames has {item}-byte elements, the output type has {esz}")
 
 
 def spk_pitch(H: int, W: int) -> int:
@@ -173,14 +208,16 @@ def spk_reconstruct(ctx, stream, H, W, T, threshold, out_frames):
 
 
 def spk_reconstruct_host(ctx, host_stream, H, W, T, threshold, host_frames):
+    if getattr(ctx, "value", None) in _CTX_FRAMES:
+        _check_host_buffers(host_stream, host_frames, H, W, T, *_CTX_FRAMES[ctx.value])
     return _check(ctx, load().spk_reconstruct_host(ctx, _addr(host_stream), H, W, T, threshold,
                                                    _addr(host_frames)))
 
 
-def spk_segments(ctx, stream, H, W, T, threshold, counts, t_start, t_end, n_int, value, cap):
-    return _check(ctx, load().spk_segments(ctx, _addr(stream), H, W, T, threshold, _addr(counts),
-                                           _addr(t_start), _addr(t_end), _addr(n_int), _addr(value),
-                                           cap))
+def spk_segments(ctx, stream, H, W, T, threshold, spike_counts, counts, t_start, t_end, n_int, value, cap):
+    return _check(ctx, load().spk_segments(ctx, _addr(stream), H, W, T, threshold, _addr(spike_counts),
+                                           _addr(counts), _addr(t_start), _addr(t_end), _addr(n_int),
+                                           _addr(value), cap))
 
 
 def spk_synchronize(ctx):
@@ -200,13 +237,16 @@ def spk_selftest_wait(ctx, limit_cycles: int):
     return _check(ctx, load().spk_selftest_wait(ctx, limit_cycles))
 
 
-def spk_reconstruct_host_noalloc(host_stream, H, W, T, threshold, host_frames, order: int = 2,
+def spk_reconstruct_host_noalloc(host_stream, H, W, T, threshold, host_frames, method: int = SPK_SSR,
                                  frame_stride: int = 1, out_dtype: int = SPK_F32, device: int = 0,
                                  stream: int | None = None, tfp_window: int = 32,
                                  stability_order: int = 3):
-    """Host-buffer reconstruction staged in the library's fixed device array (no allocation);
-    `order` is the method (1 FSR, 2 SSR, 3 TFI, 4 TFP)."""
-    cfg = spk_config(order, frame_stride, out_dtype, device, stream, tfp_window, stability_order)
+    """Host-buffer reconstruction staged in the library's fixed device array (no allocation).
+    method: 1 FSR, 2 SSR, 3 TFI, 4 TFP (window tfp_window), 5 the n-order tree
+    (stability_order levels, 3..5).  Raises ValueError, before any device work, if a buffer is
+    strided or smaller than the call reads or writes."""
+    _check_host_buffers(host_stream, host_frames, H, W, T, frame_stride, 2 if out_dtype == SPK_F16 else 4)
+    cfg = spk_config(method, frame_stride, out_dtype, device, stream, tfp_window, stability_order)
     rc = load().spk_reconstruct_host_noalloc(_c.byref(cfg), _addr(host_stream), H, W, T, threshold,
                                              _addr(host_frames))
     return _check(None, rc)
@@ -308,6 +348,8 @@ def spk_refiner_synchronize(r, stream=None):
 
 def spk_reconstruct_host_async(ctx, host_stream, H, W, T, threshold, host_frames):
     """Enqueue a host-buffer reconstruction (copies included); spk_synchronize(ctx) waits."""
+    if getattr(ctx, "value", None) in _CTX_FRAMES:
+        _check_host_buffers(host_stream, host_frames, H, W, T, *_CTX_FRAMES[ctx.value])
     return _check(ctx, load().spk_reconstruct_host_async(ctx, _addr(host_stream), H, W, T, threshold,
                                                          _addr(host_frames)))
 

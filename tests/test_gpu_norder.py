@@ -27,10 +27,11 @@ def _check(pkg, st, H, W, T, n, stride, f16=False):
                           dtype=torch.float16 if f16 else torch.float32)
     dev = torch.from_numpy(np.ascontiguousarray(st)).cuda()
     frames = R(dev, H, W, T).cpu().numpy().reshape(-1, H * W)
-    counts, ts, te, nn, v = [a.cpu().numpy() for a in R.segments(dev, H, W, T)]
+    K, counts, ts, te, nn, v = [a.cpu().numpy() for a in R.segments(dev, H, W, T, spikes=True)]
     R.synchronize()                      # raises on a device-side consistency failure
     R.close()
     r = oracle.reconstruct(st, H, W, T, 1.0, n, stride, segments=True)
+    assert np.array_equal(K, r.K)
     assert np.array_equal(counts, r.nseg)
     for p in range(H * W):
         k = counts[p]

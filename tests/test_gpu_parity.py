@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the fp64 CPU oracle.
 
-Bars: spike counts, sequence boundaries and interval counts bit-exact; fp32 values within
+Bars: spike counts K, sequence boundaries and interval counts bit-exact; fp32 values within
 1e-6 relative of the oracle; fp16 frames equal to the round-to-nearest-even of the fp32
 value and within one fp16 ulp of the oracle.
 """
@@ -45,7 +45,7 @@ def _run_gpu(torch, st, H, W, T, order, stride, dtype, theta=1.0, segments=True)
     R = pkg.Reconstructor(order=order, stride=stride, dtype=dtype)
     dev = torch.from_numpy(np.ascontiguousarray(st)).cuda()
     frames = R(dev, H, W, T, theta)
-    seg = R.segments(dev, H, W, T, theta) if segments else None
+    seg = R.segments(dev, H, W, T, theta, spikes=True) if segments else None
     R.synchronize()
     res = frames.cpu().numpy().reshape(frames.shape[0], -1), (
         None if seg is None else [s.cpu().numpy() for s in seg])
@@ -54,7 +54,8 @@ def _run_gpu(torch, st, H, W, T, order, stride, dtype, theta=1.0, segments=True)
 
 
 def _check_segments(seg, r, P):
-    counts, ts, te, n, v = seg
+    K, counts, ts, te, n, v = seg
+    assert np.array_equal(K, r.K), "spike counts differ"
     assert np.array_equal(counts, r.nseg), "sequence counts differ"
     cap = ts.shape[0]
     assert cap >= r.nseg.max(initial=0)
@@ -99,7 +100,8 @@ def test_golden_cases(torch_cuda, case):
     st = spkgen.pack(bits)
     frames, seg = _run_gpu(torch_cuda, st, 1, 300, T, case["order"], case["stride"],
                            torch_cuda.float32)
-    counts, ts, te, n, v = seg
+    K, counts, ts, te, n, v = seg
+    assert K[257] == len(case["spikes"]) and np.all(K[np.arange(300) != 257] == 0)
     k = counts[257]
     got = list(zip(ts[:k, 257].tolist(), te[:k, 257].tolist(), n[:k, 257].tolist()))
     assert got == case["segments"]
@@ -187,10 +189,12 @@ def test_large_1000x1000x20000_sampled(torch_cuda):
     f_s = frames.view(frames.shape[0], -1).index_select(1, idx).cpu().numpy()
     del frames
     torch.cuda.empty_cache()
-    counts, ts, te, n, v = R.segments(dev, w.H, w.W, w.T, 1.0)
+    K, counts, ts, te, n, v = R.segments(dev, w.H, w.W, w.T, 1.0, spikes=True)
     R.synchronize()
+    assert np.array_equal(K.cpu().numpy(), r_all.K)
     assert np.array_equal(counts.cpu().numpy(), r_all.nseg)
-    seg = [counts.cpu().numpy()[pix]] + [a.index_select(1, idx).cpu().numpy() for a in (ts, te, n, v)]
+    seg = [K.cpu().numpy()[pix], counts.cpu().numpy()[pix]] + [a.index_select(1, idx).cpu().numpy()
+                                                                for a in (ts, te, n, v)]
     R.close()
     _check_segments(seg, r, len(pix))
     _check_frames(f_s, r.frames, "f16")
@@ -211,3 +215,26 @@ def test_record_ring_overflow(torch_cuda, order, stride, dtype):
             bits[(t % 4 == 0) | (t % 4 == 1), p] = 1     # intervals 1, 3, 1, 3, ...
             bits[: p % 11, p] = 0                         # stagger the lanes
     _case(torch_cuda, spkgen.pack(bits), 1, W, T, order, stride, dtype)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_spike_counts_few_spikes(torch_cuda, order):
+    """K of pixels with no spike, one spike (first, middle or last step), two spikes, a spike
+    every step and random densities equals the number of set bits of the pixel's column
+    (Def. 2: S_1 has K - 1 elements), and the oracle's K; pixels with K < 2 have no
+    sequence and read 0 in every frame."""
+    T, P = 300, 300
+    bits = (spkgen.random_bits(T, P, 0.3, seed=9)).copy()
+    bits[:, 0:40] = 0                     # K = 0
+    bits[0, 40:48] = 1                    # K = 1 at the first step
+    bits[137, 48:56] = 1                  # K = 1 in the middle
+    bits[T - 1, 56:64] = 1                # K = 1 at the last step
+    bits[[5, 250], 64:72] = 1             # K = 2
+    bits[:, 72:80] = 1                    # K = T
+    st = spkgen.pack(bits, 1, P)
+    frames, seg = _run_gpu(torch_cuda, st, 1, P, T, order, 1, torch_cuda.float32)
+    K, counts = seg[0], seg[1]
+    assert np.array_equal(K, bits.sum(axis=0))
+    assert np.array_equal(K, oracle.reconstruct(st, 1, P, T, 1.0, order, 1).K)
+    assert np.all(counts[K < 2] == 0) and np.all(counts[K >= 2] >= 1)
+    assert np.all(frames[:, K < 2] == 0)
