@@ -10,11 +10,11 @@
 //   out = plain + L4(...)[channel 0]
 // Training minimises the mean squared error to the ground-truth intensity with Adam.
 //
-// Every convolution is an implicit GEMM: a block takes 128 pixels of one image row, stages
-// the 3 x 130 pixel halo and the weights in shared memory, and each warp multiplies 32
-// pixels by all output channels with mma.m16n8k16 (bf16 in, fp32 accumulate), the nine
-// taps x input channels forming K.  The weight gradient is a GEMM over pixels (K = pixels),
-// one warp per tap.
+// Every convolution is an implicit GEMM on the 5th-generation tensor cores (tcgen05.mma,
+// bf16 in, fp32 accumulate in tensor memory): a 128-pixel output row segment is M, the
+// nine taps x input channels are K (conv3x3_kernel).  The weight gradient is a GEMM over
+// pixels (K = pixels) with M = (tap, input channel) and N = output channel
+// (wgrad_kernel), reduced over blocks in a fixed order.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -45,15 +45,7 @@ constexpr int64_t layer_w(int l) { return 9LL * COUT[l] * CIN[l]; }
 constexpr int64_t layer_off(int l) { return l == 0 ? 0 : layer_off(l - 1) + layer_w(l - 1) + COUT[l - 1]; }
 constexpr int64_t NPARAM = layer_off(NL - 1) + layer_w(NL - 1) + COUT[NL - 1];
 
-__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
-__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
 // Activations with C channels are stored as channel-chunk planes, [N][H][C/8][W][8]: the 8
 // channels of a chunk are one 16-byte cell, and one image row of one chunk is W contiguous
@@ -512,92 +504,169 @@ bool conv(cudaStream_t s, int *status, int N, int H, int W, const bf16 *X, const
     return true;
 }
 
-// dW[tap][co][ci] += sum_p X[p + tap][ci] * dZ[p][co],  dB[co] += sum_p dZ[p][co].
-// One warp per tap (9 warps); a block walks `segs` row segments of 128 pixels.
+// ------------------------------------------------------------------ weight gradient ----
+// dW[tap][co][ci] = sum_p X[p + off(tap)][ci] * dZ[p][co],  dB[co] = sum_p dZ[p][co], with
+// off(ky, kx) = (ky - 1, kx - 1) and p over every pixel of every image (K = pixels).
+//
+// On the tensor cores as D[(tap, ci)][co] = sum_k A[(tap, ci)][k] * B[co][k]: a block walks
+// row segments of 128 pixels (one K tile each) and stages, per tap, the 128 input pixels that
+// tap multiplies as CI/8 planes of [pixel][8 channels] -- the activation layout itself, so A
+// is MN-major (8 channels contiguous in a 16-byte row, 8 pixels = 8 rows = one 128-byte core
+// matrix), and the 9 taps' planes follow each other at one stride, so that M = 128 rows of
+// (tap, ci) are one descriptor.  dZ is staged the same way as B (N = CO, MN-major).  Per
+// 16-pixel K step one thread issues NT tcgen05.mma of M = 128 (taps 0-3, 4-7 and 5-8 for
+// CI = 32, whose last tile contributes only tap 8; taps 0-7 and 1-8 for CI = 16), each
+// accumulating into its own fp32 region of tensor memory for the whole block.  Stages are
+// double-buffered: a tile is staged while the tensor cores work on the previous one.  Each
+// block writes its partial sums; wgrad_reduce_kernel adds the blocks' partials in block
+// order, so the gradient is the same bit for bit on every run.
 template <int CI, int CO>
-__global__ void __launch_bounds__(288) wgrad_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ dZ,
-                                                    float *dW, float *dB, int N, int H, int W, int segs_per_block) {
-    constexpr int PP = MT + 2 + 8;  // padded pixel stride of the transposed halo
-    __shared__ __align__(16) bf16 xt[3][CI][PP];       // X transposed: [row][ci][pixel]
-    __shared__ __align__(16) bf16 zt[CO][MT + 8];      // dZ transposed: [co][pixel]
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const int tap = warp, ky = tap / 3, kx = tap % 3;
-    constexpr int MTL = CO / 16;                       // m16 tiles over co
-    constexpr int NTL = CI / 8;
-    float acc[MTL][NTL][4];
-#pragma unroll
-    for (int i = 0; i < MTL; ++i)
-#pragma unroll
-        for (int j = 0; j < NTL; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    float bsum = 0.f;
-    const int nseg_w = (W + MT - 1) / MT;
-    const int64_t total = static_cast<int64_t>(N) * H * nseg_w;
-    for (int s = 0; s < segs_per_block; ++s) {
-        const int64_t seg = static_cast<int64_t>(blockIdx.x) * segs_per_block + s;
-        if (seg >= total) break;
-        const int xs = static_cast<int>(seg % nseg_w), y = static_cast<int>((seg / nseg_w) % H);
-        const int n = static_cast<int>(seg / (static_cast<int64_t>(nseg_w) * H));
-        const int x0 = xs * MT;
-        __syncthreads();
-        for (int c = tid; c < 3 * (MT + 2) * CI; c += 288) {
-            const int r = c / ((MT + 2) * CI), rem = c % ((MT + 2) * CI), xx = rem / CI, ci = rem % CI;
-            const int yy = y + r - 1, xg = x0 - 1 + xx;
-            bf16 v = __float2bfloat16(0.f);
-            if (yy >= 0 && yy < H && xg >= 0 && xg < W) v = X[act_idx(n, yy, xg, ci, H, W, CI)];
-            xt[r][ci][xx] = v;
-        }
-        for (int c = tid; c < MT * CO; c += 288) {
-            const int xx = c / CO, co = c % CO, xg = x0 + xx;
-            bf16 v = __float2bfloat16(0.f);
-            if (xg < W) v = dZ[act_idx(n, y, xg, co, H, W, CO)];
-            zt[co][xx] = v;
-        }
-        __syncthreads();
-        if (warp < 9) {
-#pragma unroll 1
-            for (int kc = 0; kc < MT / 16; ++kc) {
-                uint32_t a[MTL][4], b[NTL][2];
-#pragma unroll
-                for (int i = 0; i < MTL; ++i) {
-                    const int r0 = i * 16 + g, r1 = r0 + 8;
-                    const int c0 = kc * 16 + 2 * t;
-                    a[i][0] = r0 < CO ? ld32(&zt[r0][c0]) : 0u;
-                    a[i][1] = r1 < CO ? ld32(&zt[r1][c0]) : 0u;
-                    a[i][2] = r0 < CO ? ld32(&zt[r0][c0 + 8]) : 0u;
-                    a[i][3] = r1 < CO ? ld32(&zt[r1][c0 + 8]) : 0u;
-                }
-#pragma unroll
-                for (int j = 0; j < NTL; ++j) {  // B(k = pixel, n = ci): pixel + kx may be odd
-                    const bf16 *col = &xt[ky][j * 8 + g][kc * 16 + 2 * t + kx];
-                    __nv_bfloat162 p0, p1;
-                    p0.x = col[0];
-                    p0.y = col[1];
-                    p1.x = col[8];
-                    p1.y = col[9];
-                    b[j][0] = *reinterpret_cast<uint32_t *>(&p0);
-                    b[j][1] = *reinterpret_cast<uint32_t *>(&p1);
-                }
-#pragma unroll
-                for (int i = 0; i < MTL; ++i)
-#pragma unroll
-                    for (int j = 0; j < NTL; ++j) mma_bf16(acc[i][j], a[i], b[j]);
-            }
-        }
-        if (tid < CO)
-            for (int xx = 0; xx < MT; ++xx) bsum += __bfloat162float(zt[tid][xx]);
+struct WgSmem {
+    static constexpr int CH = CI / 8, CHO = CO / 8;
+    static constexpr int PLANE = MT * 16;                 // 128 pixels x 16 bytes
+    static constexpr int A_BYTES = 9 * CH * PLANE;        // the taps' input planes
+    static constexpr int B_BYTES = CHO * PLANE;           // dZ planes
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BAR_OFF = 2 * STAGE;             // mma_done[2], done
+    static constexpr int TMEM_OFF = BAR_OFF + 8 * 3;
+    static constexpr int BYTES = TMEM_OFF + 16 + 128;     // + 128 to align the base
+    static constexpr int NT = CI == 32 ? 3 : 2;           // M = 128 tiles over (tap, ci)
+    static constexpr int TPT = 128 / CI;                  // taps per tile
+    static constexpr int COLS = NT * CO;
+    static constexpr int TCOLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : 256;
+    __host__ __device__ static constexpr int tap0(int a) { return a == 0 ? 0 : a == NT - 1 ? 9 - TPT : TPT * a; }
+};
+constexpr int WG_THREADS = 256;
+constexpr int WG_MMA_TID = 128;   // warp 4, lane 0: issues the MMAs
+
+// instruction descriptor of kind::f16 with both operands MN-major (transpose bits 15, 16)
+__host__ __device__ constexpr uint32_t mma_idesc_mn(int M, int N) { return mma_idesc(M, N) | (1u << 15) | (1u << 16); }
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(WG_THREADS, 1)
+    wgrad_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ dZ, float *partial, int N, int H, int W,
+                 int *status) {
+    using L = WgSmem<CI, CO>;
+    constexpr int CH = L::CH, CHO = L::CHO, NT = L::NT;
+    constexpr uint32_t IDESC = mma_idesc_mn(128, CO);
+    constexpr int NW = 9 * CO * CI;  // weights per block partial, then CO biases
+    extern __shared__ unsigned char smraw_[];
+    unsigned char *smraw = smraw_ + ((128 - (smem_u32(smraw_) & 127)) & 127);
+    const uint32_t sbase = smem_u32(smraw);
+    uint64_t *mma_done = reinterpret_cast<uint64_t *>(smraw + L::BAR_OFF);
+    uint64_t *done = mma_done + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smraw + L::TMEM_OFF);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        mbar_init(&mma_done[0], 1);
+        mbar_init(&mma_done[1], 1);
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(L::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int nxs = (W + MT - 1) / MT;
+    const int64_t ntile = static_cast<int64_t>(N) * H * nxs;
+    float bsum = 0.f;  // thread co < CO: its bias gradient over this block's pixels, in tile order
+    bool ok = true;
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x, ++it) {
+        const int st = it & 1;
+        // the stage's previous tile (two back) must have left the tensor cores
+        if (it >= 2 && !mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1, status)) ok = false;
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        const int xs = static_cast<int>(tile % nxs), y = static_cast<int>((tile / nxs) % H);
+        const int n = static_cast<int>(tile / (static_cast<int64_t>(nxs) * H));
+        const int x0 = xs * MT;
+        const uint32_t sa = sbase + st * L::STAGE, sb = sa + L::A_BYTES;
+        for (int c = tid; c < 9 * CH * MT; c += WG_THREADS) {  // plane (tap, chunk), pixel j
+            const int j = c % MT, rest = c / MT, ch = rest % CH, tap = rest / CH;
+            const int yy = y + tap / 3 - 1, xx = x0 + tap % 3 - 1 + j;
+            const bool v = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            cp_async16(sa + (tap * CH + ch) * L::PLANE + j * 16, v ? X + act_idx(n, yy, xx, ch * 8, H, W, CI) : X, v);
+        }
+        for (int c = tid; c < CHO * MT; c += WG_THREADS) {
+            const int j = c % MT, ch = c / MT, xx = x0 + j;
+            const bool v = xx < W;
+            cp_async16(sb + ch * L::PLANE + j * 16, v ? dZ + act_idx(n, y, xx, ch * 8, H, W, CO) : dZ, v);
+        }
+        cp_async_commit();
+        cp_async_wait0();
+        fence_proxy_async_smem();  // the staged planes become visible to the tensor cores
+        __syncthreads();
+        if (tid < CO) {
+            const bf16 *zp = reinterpret_cast<const bf16 *>(smraw + st * L::STAGE + L::A_BYTES) +
+                             (tid / 8) * (L::PLANE / 2) + (tid & 7);
+            for (int j = 0; j < MT; ++j) bsum += __bfloat162float(zp[j * 8]);
+        }
+        if (tid == WG_MMA_TID) {
+            tc_fence_after();
 #pragma unroll
-    for (int i = 0; i < MTL; ++i)
+            for (int a = 0; a < NT; ++a) {
 #pragma unroll
-        for (int j = 0; j < NTL; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int co = i * 16 + g + (e >= 2 ? 8 : 0), ci = j * 8 + 2 * t + (e & 1);
-                if (co < CO) atomicAdd(&dW[(static_cast<int64_t>(tap) * CO + co) * CI + ci], acc[i][j][e]);
+                for (int s = 0; s < MT / 16; ++s) {
+                    // K step s: pixels 16 s .. 16 s + 15 = two 128-byte core matrices further
+                    const uint64_t ad = smem_desc(sa + L::tap0(a) * CH * L::PLANE + s * 256, 128, L::PLANE);
+                    const uint64_t bd = smem_desc(sb + s * 256, 128, L::PLANE);
+                    mma_bf16_tc(tmem + static_cast<uint32_t>(a * CO), ad, bd, IDESC, (it > 0 || s > 0) ? 1u : 0u);
+                }
             }
-    if (tid < CO) atomicAdd(&dB[tid], bsum);
+            mma_commit(&mma_done[st]);
+        }
+    }
+    // every MMA this block issued has completed once `done` arrives
+    if (tid == WG_MMA_TID) mma_commit(done);
+    const bool fin = mbar_wait(done, 0, status);
+    ok = __syncthreads_and(ok && fin);
+    tc_fence_after();
+    float *pw = partial + static_cast<int64_t>(blockIdx.x) * (NW + CO);
+    if (warp < 4) {  // warp w reads tensor-memory lanes 32 w .. 32 w + 31: rows (tap, ci)
+        const int m = warp * 32 + lane, tl = m / CI, ci = m % CI;
+#pragma unroll
+        for (int a = 0; a < NT; ++a) {
+            float v[CO];
+#pragma unroll
+            for (int c = 0; c < CO; c += 16)
+                tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(a * CO + c), v + c);
+            tmem_wait_ld();
+            // the last tile overlaps the one before it: it contributes its last tap only
+            if (a == NT - 1 && NT > 1 && tl != L::TPT - 1) continue;
+            const int tap = L::tap0(a) + tl;
+#pragma unroll
+            for (int co = 0; co < CO; ++co)
+                pw[(static_cast<int64_t>(tap) * CO + co) * CI + ci] = (ok && it > 0) ? v[co] : 0.f;
+        }
+    }
+    if (tid < CO) pw[NW + tid] = bsum;
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TCOLS) : "memory");
+    }
+}
+
+// g[i] = sum over blocks b = 0 .. nb-1, in that order, of partial[b][i]: a fixed order, so
+// the weight and bias gradients do not depend on scheduling
+__global__ void wgrad_reduce_kernel(const float *__restrict__ partial, int nb, int n, float *g) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nb; ++b) s += partial[static_cast<int64_t>(b) * n + i];
+        g[i] = s;
+    }
 }
 
 // out - gt -> loss sum and dZ of the last layer (bf16, 16 channels, channel 0 only)
@@ -672,6 +741,8 @@ struct spk_refiner {
     bf16 *act[NL];             // activations of layers 0..3 (act[4] unused) [N][H][4][W][8]
     bf16 *grad[2];             // two ping-pong gradient buffers, same layout
     float *out;                // training forward output
+    float *partial;            // weight-gradient partial sums, one row per block: [sms][9*32*32 + 32]
+    int sms;                   // multiprocessors: the weight-gradient grid
     int64_t cap;               // pixels the buffers hold
     int64_t steps;             // Adam steps taken
     char msg[256];
@@ -736,6 +807,26 @@ int ensure_buffers(spk_refiner *r, int64_t pixels, bool train) {
     return SPK_OK;
 }
 
+// weight and bias gradient of one layer into g (its W block, then its biases): one block per
+// multiprocessor walks the row segments, then the partial sums are added in block order
+template <int CI, int CO>
+bool wgrad(spk_refiner *r, cudaStream_t s, const bf16 *X, const bf16 *dZ, int N, int H, int W, float *g) {
+    constexpr int bytes = WgSmem<CI, CO>::BYTES;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(wgrad_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess)
+            return false;
+        attr = true;
+    }
+    const int64_t ntile = static_cast<int64_t>(N) * H * ((W + MT - 1) / MT);
+    const int grid = static_cast<int>(std::min<int64_t>(ntile, r->sms));
+    wgrad_kernel<CI, CO><<<grid, WG_THREADS, bytes, s>>>(X, dZ, r->partial, N, H, W, r->status);
+    constexpr int n = 9 * CI * CO + CO;
+    wgrad_reduce_kernel<<<(n + 255) / 256, 256, 0, s>>>(r->partial, grid, n, g);
+    return true;
+}
+
 // forward through all layers; for training the activations of L0..L3 stay in r->act[0..3]
 // (the backward pass reads them), for inference two of them are used in turn
 int forward(spk_refiner *r, cudaStream_t s, const bf16 *x0, const float *plain, int N, int H, int W, float *out,
@@ -779,6 +870,8 @@ int spk_refiner_create(int device, uint64_t seed, spk_refiner **out) {
     bool ok = true;
     for (float **p : {&r->w, &r->m, &r->v, &r->g}) ok &= cudaMalloc(p, NPARAM * sizeof(float)) == cudaSuccess;
     ok &= cudaMalloc(&r->loss, sizeof(float)) == cudaSuccess;
+    ok &= cudaDeviceGetAttribute(&r->sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && r->sms > 0;
+    ok &= ok && cudaMalloc(&r->partial, static_cast<size_t>(r->sms) * (9 * 32 * 32 + 32) * sizeof(float)) == cudaSuccess;
     ok &= cudaMalloc(&r->status, sizeof(int)) == cudaSuccess && cudaMemset(r->status, 0, sizeof(int)) == cudaSuccess;
     for (int l = 0; l < NL; ++l) {
         ok &= cudaMalloc(&r->wt[l], layer_w(l) * sizeof(bf16)) == cudaSuccess;
@@ -819,7 +912,7 @@ int spk_refiner_destroy(spk_refiner *r) {
     if (!r) return SPK_OK;
     cudaSetDevice(r->device);
     cudaDeviceSynchronize();
-    for (float *p : {r->w, r->m, r->v, r->g, r->loss, r->out})
+    for (float *p : {r->w, r->m, r->v, r->g, r->loss, r->out, r->partial})
         if (p) cudaFree(p);
     if (r->status) cudaFree(r->status);
     for (int l = 0; l < NL; ++l) {
@@ -902,28 +995,21 @@ int spk_refiner_train_step(spk_refiner *r, void *stream, const void *x0, const f
     const bf16 *x = static_cast<const bf16 *>(x0);
     rc = forward(r, s, x, plain, N, H, W, r->out, true);
     if (rc) return rc;
-    cudaMemsetAsync(r->g, 0, NPARAM * sizeof(float), s);
     cudaMemsetAsync(r->loss, 0, sizeof(float), s);
     bf16 *dz = r->grad[0], *dz2 = r->grad[1];
     mse_grad_kernel<<<512, 256, 0, s>>>(r->out, gt, P, W, 1.f / static_cast<float>(P), dz, r->loss);
-    const int segs = 8;
-    const int64_t nseg = static_cast<int64_t>(N) * H * ((W + MT - 1) / MT);
-    const int wblocks = static_cast<int>((nseg + segs - 1) / segs);
     // layer 4 (linear): weight gradient, then the gradient of act[3] through ReLU
-    wgrad_kernel<32, 16><<<wblocks, 288, 0, s>>>(r->act[3], dz, r->g + layer_off(4),
-                                                 r->g + layer_off(4) + layer_w(4), N, H, W, segs);
-    bool ok = conv<16, 32, 1>(s, r->status, N, H, W, dz, r->wd[4], nullptr, dz2, r->act[3], nullptr);
+    bool ok = wgrad<32, 16>(r, s, r->act[3], dz, N, H, W, r->g + layer_off(4));
+    ok = ok && conv<16, 32, 1>(s, r->status, N, H, W, dz, r->wd[4], nullptr, dz2, r->act[3], nullptr);
     for (int l = 3; l >= 1; --l) {
         bf16 *tmp = dz;
         dz = dz2;
         dz2 = tmp;
-        wgrad_kernel<32, 32><<<wblocks, 288, 0, s>>>(r->act[l - 1], dz, r->g + layer_off(l),
-                                                     r->g + layer_off(l) + layer_w(l), N, H, W, segs);
+        ok = ok && wgrad<32, 32>(r, s, r->act[l - 1], dz, N, H, W, r->g + layer_off(l));
         ok = ok && conv<32, 32, 1>(s, r->status, N, H, W, dz, r->wd[l], nullptr, dz2, r->act[l - 1], nullptr);
     }
-    if (!ok) return rfail(r, SPK_ERR_CUDA, "refiner backward: cuTensorMapEncodeTiled failed");
-    wgrad_kernel<16, 32><<<wblocks, 288, 0, s>>>(x, dz2, r->g + layer_off(0), r->g + layer_off(0) + layer_w(0), N, H,
-                                                 W, segs);
+    ok = ok && wgrad<16, 32>(r, s, x, dz2, N, H, W, r->g + layer_off(0));
+    if (!ok) return rfail(r, SPK_ERR_CUDA, "refiner backward: kernel set-up failed");
     r->steps += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, static_cast<float>(r->steps)), c2 = 1.f - powf(b2, static_cast<float>(r->steps));

@@ -3,7 +3,8 @@
 Parameters follow the library's layout: per layer W[tap = 3 ky + kx][Cout][Cin] then
 b[Cout]; layers 16 -> 32 -> 32 -> 32 -> 32 -> 16 (ReLU after the first four), output =
 plain + channel 0 of the last layer.  `forward` rounds weights and hidden activations to
-bf16 as the kernels store them (straight through for the gradient), everything else fp32.
+bf16 as the kernels store them (straight through for the gradient) and, for training, the
+gradients the kernels store in bf16; everything else fp32.
 """
 import numpy as np
 import torch
@@ -32,10 +33,25 @@ def bf(x):
     return x.to(torch.bfloat16).to(torch.float32)
 
 
-def forward(params, x0, plain, gt=None):
+class _GradToBf16(torch.autograd.Function):
+    """Identity forward; the gradient is rounded to bf16 on the way back, as the kernels
+    store the gradient of every layer's pre-activation (and of the output) in bf16."""
+
+    @staticmethod
+    def forward(ctx, x):
+        return x.view_as(x)
+
+    @staticmethod
+    def backward(ctx, g):
+        return bf(g)
+
+
+def forward(params, x0, plain, gt=None, bf16_grads=True):
     """x0 [N][H][W][16] (fp32 holding bf16 values), plain/gt [N][H][W] fp32 numpy or torch.
 
-    Returns (out numpy [N][H][W], loss or None, grads numpy [NPARAM] or None)."""
+    With bf16_grads the gradients of the pre-activations and of the output are rounded to
+    bf16 on the way back, where the kernels store them.  Returns (out numpy [N][H][W],
+    loss or None, grads numpy [NPARAM] or None)."""
     ls = layers(np.asarray(params, dtype=np.float32))
     ws, bs = [], []
     h = torch.as_tensor(np.asarray(x0, dtype=np.float32)).permute(0, 3, 1, 2)
@@ -45,6 +61,8 @@ def forward(params, x0, plain, gt=None):
         ws.append(wq)
         bs.append(bq)
         z = F.conv2d(h, wq, bq, padding=1)
+        if gt is not None and bf16_grads and l < len(ls) - 1:
+            z = _GradToBf16.apply(z)
         if l < len(ls) - 1:
             r = torch.relu(z)
             h = r + (bf(r) - r).detach()
@@ -52,6 +70,8 @@ def forward(params, x0, plain, gt=None):
             out = z[:, 0] + torch.as_tensor(np.asarray(plain, dtype=np.float32))
     if gt is None:
         return out.detach().numpy(), None, None
+    if bf16_grads:
+        out = _GradToBf16.apply(out)
     loss = torch.mean((out - torch.as_tensor(np.asarray(gt, dtype=np.float32))) ** 2)
     loss.backward()
     g = np.zeros(NPARAM, dtype=np.float32)

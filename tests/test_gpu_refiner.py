@@ -1,6 +1,6 @@
 """Learned refiner on the GPU: features, forward, gradients and Adam against plain PyTorch
-fp32 on the CPU (tests/refnet.py), and training on simulator streams against the plain
-reconstruction (PSNR, SSIM)."""
+fp32 on the CPU (tests/refnet.py), bitwise repeatable training, and training on simulator
+streams against the plain reconstruction (PSNR, SSIM)."""
 import math
 
 import numpy as np
@@ -66,6 +66,15 @@ def test_features_exact(H, W, T, stride, theta):
     assert np.array_equal(got, _bf16_bits(planar(want)))
 
 
+# The hidden activations are stored in bf16 (a step of 2^-8 relative): where the kernels'
+# fp32 accumulation order and PyTorch's round a value to different sides of a bf16 boundary,
+# that activation differs by one bf16 step.  The forward is therefore held to one such step
+# at the scale of the correction (observed: 2.5e-3); the gradients, whose reference rounds
+# where the kernels do, to 1e-3 relative L2 (observed: 5e-5).
+FWD_TOL = 2.0 ** -8
+GRAD_TOL = 1e-3
+
+
 def _rand_case(N, H, W, seed):
     rng = np.random.default_rng(seed)
     x0 = np.zeros((N, H, W, 16), dtype=np.float32)
@@ -98,7 +107,8 @@ def test_forward_matches_reference(N, H, W):
     corr = np.abs(want - plain).max()
     assert corr > 1e-3
     err = np.abs(got - want).max()
-    assert err <= 1e-2 * corr + 1e-6, (err, corr)
+    print(f"forward N={N} H={H} W={W}: max error {err:.3e} of correction range {corr:.3e} ({err / corr:.2e})")
+    assert err <= FWD_TOL * corr + 1e-6, (err, corr)
     ref.close()
 
 
@@ -121,8 +131,30 @@ def test_gradients_and_loss_match_reference():
                 assert np.abs(gg).max() <= 1e-9
                 continue
             rel = np.linalg.norm(gg - gr) / np.linalg.norm(gr)
-            assert rel < 3e-2, (a, rel)
+            print(f"gradient block at {a}: relative L2 {rel:.2e}")
+            assert rel < GRAD_TOL, (a, rel)
     ref.close()
+
+
+def test_training_is_deterministic():
+    """Two refiners from one seed, trained with the same batches, end with identical weights
+    bit for bit: the weight gradient reduces its per-block partial sums in a fixed order."""
+    N, H, W = 4, 30, 200
+    x0, plain, gt = _rand_case(N, H, W, seed=13)
+    args = (_dev(planar(x0), torch.bfloat16), _dev(plain), _dev(gt))
+    runs = []
+    for _ in range(2):
+        r = refiner.Refiner(seed=21)
+        grads = []
+        for step in range(4):
+            r.train_step(*args, lr=1e-3, want_loss=False)
+            grads.append(r.grads())
+        runs.append((r.params(), grads))
+        r.close()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    for ga, gb in zip(runs[0][1], runs[1][1]):
+        assert np.array_equal(ga, gb)
+    assert not np.array_equal(runs[0][1][0], runs[0][1][1])   # the weights did move
 
 
 def test_adam_first_step_moves_by_lr_times_sign():
@@ -185,9 +217,8 @@ def _clip(rec, w):
 def test_training_beats_plain_on_held_out_stream():
     base = spkgen.WORKLOADS["dynamic_250x400x20000"]
     rec = pkg.Reconstructor(order=2, stride=base.stride)
-    # the weight gradient sums with fp32 atomics, so the trajectory is not bitwise repeatable:
-    # enough clips and steps that the held-out gain is stable (about 1 dB); the headline
-    # checkpoint, trained on 10^4 full-size clips, gains about 5 dB on the bench stream
+    # 12 small clips, 1500 steps: the held-out gain is about 5 dB (asserted > 0.3 dB); the
+    # headline checkpoint, trained on 10^4 full-size clips, gains about 5.7 dB on the bench stream
     clips = [_clip(rec, base.resized(H=64, W=128, T=4000, seed=s)) for s in range(21, 33)]
     test = _clip(rec, base.resized(H=64, W=128, T=4000, seed=41))
     ref = refiner.Refiner(seed=0)
@@ -227,7 +258,7 @@ def test_packaged_checkpoint_matches_reference_on_a_scene():
     want, _, _ = refnet.forward(p, xh, plain.cpu().numpy())
     got = out.cpu().numpy()
     corr = np.abs(want - plain.cpu().numpy()).max()
-    assert np.abs(got - want).max() <= 1e-2 * corr + 1e-6
+    assert np.abs(got - want).max() <= FWD_TOL * corr + 1e-6
     g = gt.reshape(w.T_out, w.H, w.W)[20:]
     assert quality.psnr(got[20:], g) > quality.psnr(plain.cpu().numpy()[20:], g) + 2.0
     ref.close()
