@@ -63,7 +63,12 @@ enum spk_dtype { SPK_F32 = 0, SPK_F16 = 1 };
  *           stable sequence of a level-k stream the '-' and '+' streams of its two values
  *           (index distances between their occurrences) are segmented by the same rule,
  *           and each of their breaks cuts the level above after the element where the
- *           breaking distance ends.  Whole streams only (no spk_stream / spk_run). */
+ *           breaking distance ends.  Whole streams only (no spk_stream / spk_run).  Cuts
+ *           of deep levels wait in a per-pixel ring (64 cuts at first, owned by the
+ *           context) until no earlier cut can appear; if a pixel needs more, the call runs
+ *           again with rings twice as large, so every valid stream is reconstructed.  For
+ *           this method spk_reconstruct and spk_segments therefore wait for the device
+ *           (synchronous) and can also return SPK_ERR_OOM. */
 enum spk_method { SPK_FSR = 1, SPK_SSR = 2, SPK_TFI = 3, SPK_TFP = 4, SPK_NORDER = 5 };
 
 typedef struct spk_config {
@@ -283,6 +288,11 @@ int spk_refiner_synchronize(spk_refiner *r, void *stream);
  * shared GPU.  n = 0 clears it.  Errors: SPK_ERR_ARG for n < 0. */
 int spk_debug_fail_allocations(int n);
 
+/* Test hook of the n-order rings (no counterpart in the paper): later SPK_NORDER calls
+ * start with rings of `cap` cuts per pixel (a power of two; 0 restores the default 64), so
+ * that the regrowth path can be exercised on small streams.  Errors: SPK_ERR_ARG. */
+int spk_debug_norder_capacity(int cap);
+
 /* Diagnostic of the bounded device waits (no counterpart in the paper).  Every wait of
  * the kernels (the mbarrier waits of the stream pipeline) gives up after a bounded time
  * (about 2 s) instead of hanging, sets the timeout bit of the context's status word and
@@ -313,9 +323,12 @@ int spk_selftest_wait(spk_ctx *ctx, int64_t limit_cycles);
  *                 (the stream must belong to cfg->device)
  *   host_stream   host, uint8 [T][spk_pitch(H, W)]
  *   host_frames   host, [T_out][H][W] of cfg->out_dtype, written completely
- * The scratch holds a 256-byte status block, the stream rounded up to 256 bytes and the
- * frames: 256 + round_up(T*pitch, 256) + T_out*H*W*sizeof(out) must not exceed
- * SPK_NOALLOC_SCRATCH_BYTES, else the call returns SPK_ERR_ARG before any device work.
+ * The scratch holds a 256-byte status block, the stream and the frames, each rounded up
+ * to 256 bytes, and for SPK_NORDER the pending-cut rings (512 bytes per pixel at first):
+ * 256 + round_up(T*pitch, 256) + round_up(T_out*H*W*sizeof(out), 256) (+ 512*H*W) must not
+ * exceed SPK_NOALLOC_SCRATCH_BYTES, else the call returns SPK_ERR_ARG before any device
+ * work.  An n-order stream whose rings must grow beyond the rest of the array returns
+ * SPK_ERR_INTERNAL (spk_reconstruct_host grows them instead).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  * with that device current); make that first call before any stream capture begins.
  * Every call shares the one array: a call clears the status word it needs, but two calls

@@ -56,6 +56,8 @@ constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz: bounded waits
 // device status bits
 constexpr int DEV_TIMEOUT = 1;
 constexpr int DEV_INTERNAL = 2;
+constexpr int DEV_PEND_FULL = 4;   // an n-order tree's pending-cut ring was too small (the host reruns)
+constexpr int NORDER_CAP0 = 64;    // initial pending-cut ring per pixel (entries, a power of two)
 
 template <int TT>
 struct Smem {
@@ -99,6 +101,8 @@ struct Batch {
     Job jobs[MAXJ];
     int njobs;
     int *status;
+    int *pend;                                  // n-order tree: pending-cut rings [P][pend_cap][2]
+    int pend_cap;
     int32_t *spikes;                            // segments mode (one job): K per pixel, or nullptr
     int32_t *counts, *seg_ts, *seg_te, *seg_n;  // segments mode: the stable sequences
     float *seg_v;
@@ -507,8 +511,12 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     // ORDER 5 is the general n-order tree (job.order_n levels); 1 FSR, 2 SSR, 3 TFI
     using Scan = std::conditional_t<ORDER == 5, spk::TreeScan, spk::PixelScan<ORDER == 5 ? 1 : ORDER>>;
     Scan sc;
-    if constexpr (ORDER == 5) sc.init(job.order_n);
-    else sc.init();
+    if constexpr (ORDER == 5) {  // the pixel's ring: pend_cap (t, i) pairs, contiguous
+        int *ring = prm.pend + static_cast<int64_t>(valid ? p : 0) * 2 * prm.pend_cap;
+        sc.init(job.order_n, ring, ring + 1, 2, prm.pend_cap);
+    } else {
+        sc.init();
+    }
 
     FrameSink<OutT> fs;
     SegSink ss;
@@ -587,8 +595,6 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     }
     if (!ok) return;
 
-    if constexpr (ORDER == 5)
-        if (valid && sc.bad) atomicOr(prm.status, DEV_INTERNAL);  // (checked again after finish)
     if constexpr (SEGMENTS) {
         sc.finish(ss);
         ss.done();
@@ -596,11 +602,15 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         // K, the number of spikes (S_1 has K - 1 elements, Def. 2): the scan's own count
         if (valid && prm.spikes) prm.spikes[p] = sc.last_t >= 0 ? sc.nint + 1 : 0;
         if constexpr (ORDER == 5)
-            if (valid && sc.bad) atomicOr(prm.status, DEV_INTERNAL);
+            if (valid && sc.bad)
+                atomicOr(prm.status, (sc.bad & spk::TREE_BAD_ORDER ? DEV_INTERNAL : 0) |
+                                         (sc.bad & spk::TREE_BAD_FULL ? DEV_PEND_FULL : 0));
     } else if (job.flags & JOB_LAST) {
         sc.finish(fs);
         if constexpr (ORDER == 5)
-            if (valid && sc.bad) atomicOr(prm.status, DEV_INTERNAL);
+            if (valid && sc.bad)
+                atomicOr(prm.status, (sc.bad & spk::TREE_BAD_ORDER ? DEV_INTERNAL : 0) |
+                                         (sc.bad & spk::TREE_BAD_FULL ? DEV_PEND_FULL : 0));
         if (valid) fs.cand(TAIL, 0);  // tail hold (0 without spans)
         flush_rows(fs, INT_MAX, valid, true);
         if (valid && fs.bad) atomicOr(prm.status, DEV_INTERNAL);
@@ -849,6 +859,7 @@ struct spk_stream {
 // (spk_debug_fail_allocations) to exercise the SPK_ERR_OOM paths without exhausting a GPU.
 namespace {
 std::atomic<int> g_fail_allocs{0};
+std::atomic<int> g_norder_cap0{NORDER_CAP0};  // first ring size of an n-order call (test hook)
 cudaError_t dev_malloc(void **p, size_t bytes) {
     int n = g_fail_allocs.load();
     while (n > 0 && !g_fail_allocs.compare_exchange_weak(n, n - 1)) {
@@ -880,6 +891,9 @@ struct spk_ctx {
     size_t lane_out_cap[2];
     cudaEvent_t lane_fence;  // orders the work already on `stream` before a lane's call
     int next_lane;
+    int *d_pend;             // n-order tree: pending-cut rings, grown on demand
+    size_t pend_bytes;
+    bool pend_fixed;         // the rings live in caller-provided memory that may not grow
     char msg[512];
 };
 
@@ -1084,7 +1098,43 @@ int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float thr
     prm.seg_n = n;
     prm.seg_v = v;
     prm.cap = cap;
-    return dispatch(ctx, prm, nb, segments, tile);
+    if (ctx->cfg.method != SPK_NORDER) return dispatch(ctx, prm, nb, segments, tile);
+
+    // The n-order tree holds cuts that are not final yet in a per-pixel ring.  A pixel whose
+    // ring runs full reports it; the call then runs again with rings twice as large, so every
+    // valid stream is reconstructed (at most T + 1 cuts can be pending).  Synchronous.
+    const int64_t P = static_cast<int64_t>(H) * W;
+    int pcap = g_norder_cap0.load();
+    for (;;) {
+        const size_t need = static_cast<size_t>(2) * static_cast<size_t>(pcap) * static_cast<size_t>(P) * sizeof(int);
+        if (need > ctx->pend_bytes) {
+            if (ctx->pend_fixed)
+                return fail(ctx, SPK_ERR_INTERNAL, "n-order pending cuts need %zu bytes of rings, %zu available", need,
+                            ctx->pend_bytes);
+            if (ctx->d_pend) cudaFree(ctx->d_pend);
+            ctx->d_pend = nullptr;
+            ctx->pend_bytes = 0;
+            if (dev_malloc(&ctx->d_pend, need) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) of the n-order pending-cut rings failed", need);
+            }
+            ctx->pend_bytes = need;
+        }
+        prm.pend = ctx->d_pend;
+        prm.pend_cap = pcap;
+        int rc = dispatch(ctx, prm, nb, segments, tile);
+        if (rc) return rc;
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+        int st = 0;
+        if (cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(ctx, SPK_ERR_CUDA, "status read failed");
+        if (st != DEV_PEND_FULL) return SPK_OK;  // done, or another failure for spk_synchronize to report
+        if (static_cast<int64_t>(pcap) > T) return fail(ctx, SPK_ERR_INTERNAL, "n-order pending cuts exceed T");
+        if (cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess)
+            return fail(ctx, SPK_ERR_CUDA, "status reset failed");
+        pcap *= 2;
+    }
 }
 
 bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
@@ -1152,6 +1202,7 @@ int spk_destroy(spk_ctx *ctx) {
     cudaFree(ctx->d_status);
     if (ctx->d_in) cudaFree(ctx->d_in);
     if (ctx->d_out) cudaFree(ctx->d_out);
+    if (ctx->d_pend) cudaFree(ctx->d_pend);
     delete ctx;
     return SPK_OK;
 }
@@ -1482,6 +1533,12 @@ int spk_debug_fail_allocations(int n) {
     return SPK_OK;
 }
 
+int spk_debug_norder_capacity(int cap) {
+    if (cap < 0 || (cap & (cap - 1))) return SPK_ERR_ARG;
+    g_norder_cap0.store(cap ? cap : NORDER_CAP0);
+    return SPK_OK;
+}
+
 int spk_reconstruct_host_async(spk_ctx *ctx, const uint8_t *host_stream, int H, int W, int T, float threshold,
                                void *host_frames) {
     int rc = check_stream_args(ctx, host_stream, H, W, T, threshold);
@@ -1573,12 +1630,15 @@ extern "C" int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t
     const int64_t P = static_cast<int64_t>(H) * W;
     const int64_t T_out = spk_num_frames(T, cfg->frame_stride);
     const size_t esz = cfg->out_dtype == SPK_F16 ? 2 : 4;
+    // the n-order tree also needs its pending-cut rings: 2 x NORDER_CAP0 ints per pixel at first
+    const double ring_d = cfg->method == SPK_NORDER ? 2.0 * NORDER_CAP0 * sizeof(int) * static_cast<double>(P) : 0.0;
     const double need_d = static_cast<double>(NOALLOC_STATUS_BYTES) +
                           static_cast<double>(round256(static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W)))) +
-                          static_cast<double>(T_out) * static_cast<double>(P) * static_cast<double>(esz);
+                          static_cast<double>(round256(static_cast<size_t>(T_out) * static_cast<size_t>(P) * esz)) +
+                          ring_d;
     if (need_d > static_cast<double>(NOALLOC_BYTES))
         return fail(nullptr, SPK_ERR_ARG,
-                    "stream + frames need %.0f bytes of device scratch; spk_reconstruct_host_noalloc has %zu "
+                    "stream, frames and rings need %.0f bytes of device scratch; spk_reconstruct_host_noalloc has %zu "
                     "(use spk_reconstruct_host for larger problems)",
                     need_d, NOALLOC_BYTES);
     const size_t in_bytes = static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W));
@@ -1611,6 +1671,12 @@ extern "C" int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t
     tmp.tile = TT_DEFAULT;
     tmp.stream = static_cast<cudaStream_t>(cfg->stream);
     tmp.d_status = d_status;
+    if (cfg->method == SPK_NORDER) {  // the rest of the array holds the rings (no allocation)
+        const size_t used = NOALLOC_STATUS_BYTES + round256(in_bytes) + round256(out_bytes);
+        tmp.d_pend = reinterpret_cast<int *>(base + used);
+        tmp.pend_bytes = NOALLOC_BYTES - used;
+        tmp.pend_fixed = true;
+    }
     // A failure after the first enqueue waits for what was enqueued, so that no copy still
     // reads host_stream (or writes the array) once the call has returned.
     auto bail = [&](int code) {

@@ -190,10 +190,14 @@ struct PixelScan {
 // Cuts of deep nodes lie arbitrarily far in the past, so they wait, sorted and without
 // duplicates, in a per-pixel list until they are final: a node can only emit the cut of
 // its latest element, so every cut at or before the minimum of those over the nodes with
-// an open sequence (frontier()) is final and goes to the sink in order.
+// an open sequence (frontier()) is final and goes to the sink in order.  The list is a
+// ring of pcap entries (a power of two) in storage the caller provides, entry j of slot s
+// at pt[s * ps], pi[s * ps]; a push that finds it full sets bad bit 2 (the caller runs the
+// pixel again with a larger ring), an ordering fault bad bit 1.
 constexpr int TREE_MAX = 5;                       // deepest order
 constexpr int TREE_NODES = (1 << TREE_MAX) - 1;
-constexpr int TREE_PEND = 48;                     // pending cuts per pixel
+constexpr int TREE_BAD_ORDER = 1;
+constexpr int TREE_BAD_FULL = 2;
 
 struct TreeScan {
     int n;                      // order (number of levels)
@@ -203,11 +207,13 @@ struct TreeScan {
     int q0[TREE_NODES], q1[TREE_NODES];  // last occurrence (node element index) of v0 / v1, -1: none
     int jn[TREE_NODES];         // next element index of the node's stream
     int pct[TREE_NODES], pci[TREE_NODES];  // cut after the node's latest element
-    int pt[TREE_PEND], pi[TREE_PEND], np;  // pending cuts, increasing t
+    int *pt, *pi;               // pending cuts, increasing t: a ring in the caller's storage
+    int ps, pcap;               // its slot stride and capacity (a power of two)
+    int ph, np;                 // first slot and number of pending cuts
     int rel_t;                  // last cut handed to the sink
-    int bad;                    // pending list overflowed, or a cut arrived behind the frontier
+    int bad;                    // TREE_BAD_FULL: the ring was too small; TREE_BAD_ORDER: a cut arrived behind the frontier
 
-    SPK_DEV void init(int order) {
+    SPK_DEV void init(int order, int *pend_t, int *pend_i, int stride, int cap) {
         n = order;
         last_t = -1;
         nint = 0;
@@ -216,9 +222,16 @@ struct TreeScan {
             q0[k] = q1[k] = -1;
             jn[k] = 0;
         }
-        np = 0;
+        pt = pend_t;
+        pi = pend_i;
+        ps = stride;
+        pcap = cap;
+        ph = np = 0;
         rel_t = -1;
         bad = 0;
+    }
+    SPK_DEV int64_t slot(int j) const {  // storage index of the j-th pending cut
+        return static_cast<int64_t>((ph + j) & (pcap - 1)) * ps;
     }
     SPK_DEV void first_spike(int t) { last_t = t; }
 
@@ -263,22 +276,24 @@ struct TreeScan {
     }
     SPK_DEV void push(int t, int i) {
         if (t <= rel_t) {               // handed over already (equal) -- earlier would be a fault
-            if (t < rel_t) bad = 1;
+            if (t < rel_t) bad |= TREE_BAD_ORDER;
             return;
         }
         int j = np;
-        while (j > 0 && pt[j - 1] > t) --j;
-        if (j > 0 && pt[j - 1] == t) return;  // the same cut from two levels
-        if (np == TREE_PEND) {
-            bad = 1;
+        while (j > 0 && pt[slot(j - 1)] > t) --j;
+        if (j > 0 && pt[slot(j - 1)] == t) return;  // the same cut from two levels
+        if (np == pcap) {
+            bad |= TREE_BAD_FULL;
             return;
         }
         for (int m = np; m > j; --m) {
-            pt[m] = pt[m - 1];
-            pi[m] = pi[m - 1];
+            const int64_t a = slot(m), b = slot(m - 1);
+            pt[a] = pt[b];
+            pi[a] = pi[b];
         }
-        pt[j] = t;
-        pi[j] = i;
+        const int64_t s = slot(j);
+        pt[s] = t;
+        pi[s] = i;
         ++np;
     }
     // the sequences of every descendant of node k (at `level`) end
@@ -336,18 +351,14 @@ struct TreeScan {
     // hand every final pending cut to the sink, in time order
     template <class Sink>
     SPK_DEV void release(Sink &sink, int S) {
-        int m = 0;
-        while (m < np && pt[m] <= S) {
-            sink.cand(pt[m], pi[m]);
-            rel_t = pt[m];
-            ++m;
-        }
-        if (m) {
-            for (int j = m; j < np; ++j) {
-                pt[j - m] = pt[j];
-                pi[j - m] = pi[j];
-            }
-            np -= m;
+        while (np > 0) {
+            const int64_t s = slot(0);
+            const int t = pt[s];
+            if (t > S) break;
+            sink.cand(t, pi[s]);
+            rel_t = t;
+            ph = (ph + 1) & (pcap - 1);
+            --np;
         }
     }
     template <class Sink>

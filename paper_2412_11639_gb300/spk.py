@@ -24,7 +24,7 @@ EXPORTS = ("spk_create", "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reco
            "spk_refiner_create", "spk_refiner_destroy", "spk_refiner_last_error",
            "spk_refiner_set_params", "spk_refiner_get_params", "spk_refiner_forward",
            "spk_refiner_train_step", "spk_refiner_synchronize", "spk_reconstruct_host_async",
-           "spk_debug_fail_allocations")
+           "spk_debug_fail_allocations", "spk_debug_norder_capacity")
 SPK_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -118,6 +118,8 @@ def load(path: str | None = None):
     lib.spk_refiner_synchronize.restype = i32
     lib.spk_debug_fail_allocations.argtypes = [i32]
     lib.spk_debug_fail_allocations.restype = i32
+    lib.spk_debug_norder_capacity.argtypes = [i32]
+    lib.spk_debug_norder_capacity.restype = i32
     lib.spk_selftest_wait.argtypes = [vp, i64]
     lib.spk_selftest_wait.restype = i32
     lib.spk_reconstruct_host_noalloc.argtypes = [_c.POINTER(spk_config), vp, i32, i32, i32, f32, vp]
@@ -357,3 +359,8 @@ def spk_reconstruct_host_async(ctx, host_stream, H, W, T, threshold, host_frames
 def spk_debug_fail_allocations(n: int):
     """Make the library's next n device allocations fail (test hook of the SPK_ERR_OOM paths)."""
     return _check(None, load().spk_debug_fail_allocations(n))
+
+
+def spk_debug_norder_capacity(cap: int):
+    """First pending-cut ring size (cuts per pixel) of later n-order calls; 0 restores 64."""
+    return _check(None, load().spk_debug_norder_capacity(cap))

@@ -91,13 +91,16 @@ int run(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, FILE *ou
 
 // The general n-order tree (orders 3..5), driven as the kernel drives it: after every word
 // the final pending cuts go to the sink in time order (release); they must arrive strictly
-// increasing and the tree's own overflow flag must stay clear.
-int run_tree(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, int n, FILE *out) {
+// increasing and the tree's ordering flag must stay clear.  The pending-cut ring holds
+// `cap` cuts; a pixel that needs more sets the tree's full flag (exit status 4), and the
+// largest number of cuts pending at a word end over all pixels goes to stderr.
+int run_tree(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, int n, int cap, FILE *out) {
     std::vector<int32_t> counts(P, 0), spans;
-    int bad = 0;
-    auto *sc = new spk::TreeScan;  // about 1.4 KB of node arrays
+    std::vector<int> pend_t(cap), pend_i(cap);
+    int bad = 0, max_np = 0;
+    auto *sc = new spk::TreeScan;  // about 1 KB of node arrays
     for (int64_t p = 0; p < P; ++p) {
-        sc->init(n);
+        sc->init(n, pend_t.data(), pend_i.data(), 1, cap);
         Cuts c;
         int t0 = -1;
         for (int base = 0; base < T; base += 32) {
@@ -115,10 +118,12 @@ int run_tree(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, int
                 w &= w - 1;
                 sc->spike(base + b, c);
             }
+            if (sc->np > max_np) max_np = sc->np;
             sc->release(c);
         }
         sc->finish(c);
-        if (sc->bad) bad |= 4;
+        if (sc->bad & spk::TREE_BAD_ORDER) bad |= 1;
+        if (sc->bad & spk::TREE_BAD_FULL) bad |= 4;
         for (size_t j = 1; j < c.t.size(); ++j)
             if (c.t[j] <= c.t[j - 1]) bad |= 1;
         int ct = t0, ci = -1;
@@ -132,6 +137,7 @@ int run_tree(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, int
         counts[p] = static_cast<int32_t>(c.t.size());
     }
     delete sc;
+    fprintf(stderr, "max_pending %d\n", max_np);
     fwrite(counts.data(), sizeof(int32_t), counts.size(), out);
     fwrite(spans.data(), sizeof(int32_t), spans.size(), out);
     return bad;
@@ -140,8 +146,13 @@ int run_tree(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, int
 }  // namespace
 
 int main(int argc, char **argv) {
-    if (argc != 7) {
-        fprintf(stderr, "usage: scan_host stream.bin P T pitch order out.bin\n");
+    if (argc != 7 && argc != 8) {
+        fprintf(stderr, "usage: scan_host stream.bin P T pitch order out.bin [ring capacity, orders 3..5]\n");
+        return 2;
+    }
+    const int cap = argc == 8 ? atoi(argv[7]) : 1 << 16;
+    if (cap < 1 || (cap & (cap - 1))) {
+        fprintf(stderr, "the ring capacity must be a power of two\n");
         return 2;
     }
     const int64_t P = atoll(argv[2]), pitch = atoll(argv[4]);
@@ -155,10 +166,10 @@ int main(int argc, char **argv) {
     if (order < 1 || order > spk::TREE_MAX) return 2;
     const int bad = order == 1   ? run<1>(s, P, T, pitch, out)
                     : order == 2 ? run<2>(s, P, T, pitch, out)
-                                 : run_tree(s, P, T, pitch, order, out);
+                                 : run_tree(s, P, T, pitch, order, cap, out);
     fclose(out);
     if (bad)
         fprintf(stderr, "property failed: %s%s%s\n", bad & 1 ? "order " : "", bad & 2 ? "frontier " : "",
-                bad & 4 ? "tree pending list" : "");
-    return bad ? 3 : 0;
+                bad & 4 ? "tree pending ring full" : "");
+    return bad == 4 ? 4 : bad ? 3 : 0;
 }

@@ -100,3 +100,26 @@ def test_norder_runs_whole_streams_only(env):
     with pytest.raises(spk.SpkError):
         env.spk_run(R.ctx, [(dev, 4, 8, 100, 1.0, out, None)])
     R.close()
+
+
+@pytest.mark.parametrize("n", [3, 5])
+def test_norder_rings_regrow(env, n):
+    """Deep cuts wait in per-pixel rings; started with rings of 2 cuts, a call whose pixels
+    need more runs again with rings twice as large until they fit, and the frames and
+    sequences still equal the oracle's (the regrowth is visible as extra launches)."""
+    from paper_2412_11639_gb300 import spk
+    w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=12, W=70, T=3000)
+    st, _ = spkgen.make_stream(w)
+    spk.spk_debug_norder_capacity(2)
+    try:
+        R = env.Reconstructor(order=5, stability_order=n, stride=w.stride)
+        dev = torch.from_numpy(np.ascontiguousarray(st)).cuda()
+        n0 = spk.spk_launch_count(R.ctx)
+        frames = R(dev, w.H, w.W, w.T).cpu().numpy().reshape(-1, w.P)
+        R.synchronize()
+        assert spk.spk_launch_count(R.ctx) - n0 >= 3       # 2 -> 4 -> 8 ... cuts per pixel
+        R.close()
+        r = _check(env, st, w.H, w.W, w.T, n, w.stride)
+        assert np.all(np.abs(frames - r.frames) <= REL_TOL * np.abs(r.frames))
+    finally:
+        spk.spk_debug_norder_capacity(0)

@@ -29,12 +29,12 @@ def scan_host(tmp_path_factory):
     return exe
 
 
-def run_host(exe, tmp_path, st, P, T, order):
+def run_host(exe, tmp_path, st, P, T, order, ring=None):
     st = np.ascontiguousarray(st, dtype=np.uint8)
     src, dst = tmp_path / "stream.bin", tmp_path / "spans.bin"
     st.tofile(src)
-    r = subprocess.run([exe, str(src), str(P), str(T), str(st.shape[1]), str(order), str(dst)],
-                       capture_output=True, text=True, timeout=600)
+    r = subprocess.run([exe, str(src), str(P), str(T), str(st.shape[1]), str(order), str(dst)]
+                       + ([str(ring)] if ring else []), capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     raw = np.fromfile(dst, dtype=np.int32)
     counts = raw[:P]
@@ -108,3 +108,27 @@ def test_tree_equals_oracle_on_random_bits(scan_host, tmp_path, density, order):
     bits = spkgen.random_bits(T, H * W, density, seed=int(density * 1000) + 10 * order)
     st = spkgen.pack(bits, H, W)
     check_against_oracle(scan_host, tmp_path, st, H, W, T, order)
+
+
+@pytest.mark.parametrize("order", [3, 5])
+def test_tree_ring_reports_full_and_large_ring_is_exact(scan_host, tmp_path, order):
+    """The tree's pending-cut ring: a ring too small for a scene's deep cuts sets the full
+    flag (exit status 4) instead of dropping cuts silently, and the largest number pending
+    is reported; a ring of that size (rounded up to a power of two) reproduces the oracle."""
+    w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=12, W=40, T=2500)
+    st, _ = spkgen.make_stream(w)
+    st = np.ascontiguousarray(st, dtype=np.uint8)
+    src, dst = tmp_path / "stream.bin", tmp_path / "spans.bin"
+    st.tofile(src)
+    args = [scan_host, str(src), str(w.P), str(w.T), str(st.shape[1]), str(order), str(dst)]
+    big = subprocess.run(args + [str(1 << 16)], capture_output=True, text=True, timeout=600)
+    assert big.returncode == 0, big.stderr
+    need = int(big.stderr.split("max_pending")[1].split()[0])
+    assert need > 4
+    small = subprocess.run(args + ["2"], capture_output=True, text=True, timeout=600)
+    assert small.returncode == 4, small.stderr
+    ring = 1 << (need - 1).bit_length()
+    ref = oracle.reconstruct(st, w.H, w.W, w.T, 1.0, order, 1, frames=False, segments=True)
+    counts, spans = run_host(scan_host, tmp_path, st, w.P, w.T, order, ring=ring)
+    assert np.array_equal(counts, ref.nseg)
+    assert np.array_equal(spans[:, 1], ref.seg_te)
