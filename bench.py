@@ -43,7 +43,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dynamic_250x400x20000")
     ap.add_argument("--T", type=int, default=0,
-                    help="cut the workload to its first T steps (profiling a smaller case)")
+                    help="cut the workload (refine mode: the evaluation stream) to its first T steps "
+                         "(profiling a smaller case)")
     ap.add_argument("--rows", type=int, default=0,
                     help="reconstruct only the first ROWS rows of the same stream (fewer blocks "
                          "per SM: shows whether the scan is bound per warp or per SM)")
@@ -488,9 +489,12 @@ REFINER_MACS = 9 * (5 * 32 + 3 * 32 * 32 + 32 * 1)
 REFINER_MACS_PADDED = 9 * (16 * 32 + 3 * 32 * 32 + 32 * 16)
 
 
-def refiner_eval(ref, rec, w, chunk: int = 100, reps: int = 3, ssim_every: int = 20, skip: int = 20):
+def refiner_eval(ref, rec, w, chunk: int = 0, reps: int = 3, ssim_every: int = 20, skip: int = 20):
     """Refined vs plain frames of workload w against its ground truth, and the refiner's
-    device throughput (features + forward) with CUDA events."""
+    device throughput (features + forward) with CUDA events.  chunk: frames per forward
+    call (0: all frames in one call, the fastest; smaller chunks leave SMs idle at the end of
+    every layer)."""
+    chunk = chunk or w.T_out
     import numpy as np
     import torch
 
@@ -565,6 +569,8 @@ def run_refine(args):
     import spkgen
     from paper_2412_11639_gb300 import refiner
     base = spkgen.WORKLOADS["dynamic_250x400x20000"]
+    if args.T:                           # evaluate on the stream's first T steps (profiling)
+        base = base.resized(T=args.T, name=f"{base.name}[:{args.T}]")
     rec = pkg.Reconstructor(order=2, stride=base.stride)
     ref = refiner.Refiner(seed=0)
     if args.refine_clips == 0:           # evaluate (and time) the committed checkpoint

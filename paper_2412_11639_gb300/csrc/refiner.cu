@@ -78,7 +78,7 @@ __host__ __device__ __forceinline__ int64_t act_idx(int n, int y, int x, int c, 
 // mbarrier) after the last MMA that reads it; four warps read finished accumulators out of
 // tensor memory and write the output rows.  Loads, MMAs and the write-out of different rows
 // overlap.
-constexpr int RY = 16;  // output rows per task
+constexpr int RY = 32;  // output rows per task
 constexpr long long MMA_WAIT_CYCLES = 4000000000LL;  // ~2 s: bounded waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
