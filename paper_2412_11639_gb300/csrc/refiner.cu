@@ -517,7 +517,8 @@ bool conv(cudaStream_t s, int *status, int N, int H, int W, const bf16 *X, const
 // 16-pixel K step one thread issues NT tcgen05.mma of M = 128 (taps 0-3, 4-7 and 5-8 for
 // CI = 32, whose last tile contributes only tap 8; taps 0-7 and 1-8 for CI = 16), each
 // accumulating into its own fp32 region of tensor memory for the whole block.  Stages are
-// double-buffered: a tile is staged while the tensor cores work on the previous one.  Each
+// double-buffered: the next tile's cp.async loads are in flight while the tensor cores and
+// the bias sums (all threads, pixel groups added in a fixed order) work on this one.  Each
 // block writes its partial sums; wgrad_reduce_kernel adds the blocks' partials in block
 // order, so the gradient is the same bit for bit on every run.
 template <int CI, int CO>
@@ -527,7 +528,8 @@ struct WgSmem {
     static constexpr int A_BYTES = 9 * CH * PLANE;        // the taps' input planes
     static constexpr int B_BYTES = CHO * PLANE;           // dZ planes
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int BAR_OFF = 2 * STAGE;             // mma_done[2], done
+    static constexpr int RED_OFF = 2 * STAGE;             // bias partial sums, WG_THREADS floats
+    static constexpr int BAR_OFF = RED_OFF + 256 * 4;     // mma_done[2], done
     static constexpr int TMEM_OFF = BAR_OFF + 8 * 3;
     static constexpr int BYTES = TMEM_OFF + 16 + 128;     // + 128 to align the base
     static constexpr int NT = CI == 32 ? 3 : 2;           // M = 128 tiles over (tap, ci)
@@ -578,16 +580,10 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     const int nxs = (W + MT - 1) / MT;
     const int64_t ntile = static_cast<int64_t>(N) * H * nxs;
     float bsum = 0.f;  // thread co < CO: its bias gradient over this block's pixels, in tile order
-    bool ok = true;
-    int it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x, ++it) {
-        const int st = it & 1;
-        // the stage's previous tile (two back) must have left the tensor cores
-        if (it >= 2 && !mbar_wait(&mma_done[st], ((it - 2) >> 1) & 1, status)) ok = false;
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
+    float *red = reinterpret_cast<float *>(smraw + L::RED_OFF);  // [WG_THREADS / CO][CO] partial sums
+    constexpr int PARTS = WG_THREADS / CO, PPX = MT / PARTS;     // pixel groups of the bias sum
+    // cp.async of one tile into stage st: the 9 taps' input planes, then the dZ planes
+    auto stage_tile = [&](int64_t tile, int st) {
         const int xs = static_cast<int>(tile % nxs), y = static_cast<int>((tile / nxs) % H);
         const int n = static_cast<int>(tile / (static_cast<int64_t>(nxs) * H));
         const int x0 = xs * MT;
@@ -603,15 +599,27 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
             const bool v = xx < W;
             cp_async16(sb + ch * L::PLANE + j * 16, v ? dZ + act_idx(n, y, xx, ch * 8, H, W, CO) : dZ, v);
         }
+    };
+    bool ok = true;
+    int it = 0;
+    if (static_cast<int64_t>(blockIdx.x) < ntile) stage_tile(blockIdx.x, 0);
+    cp_async_commit();
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x, ++it) {
+        const int st = it & 1;
+        const int64_t next = tile + gridDim.x;
+        // the next tile goes to the other stage once the tile before this one has left the
+        // tensor cores; its loads then overlap this tile's MMAs and bias sums
+        if (next < ntile && it >= 1 && !mbar_wait(&mma_done[st ^ 1], ((it - 1) >> 1) & 1, status)) ok = false;
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        if (next < ntile) stage_tile(next, st ^ 1);
         cp_async_commit();
-        cp_async_wait0();
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this tile's group has landed
         fence_proxy_async_smem();  // the staged planes become visible to the tensor cores
         __syncthreads();
-        if (tid < CO) {
-            const bf16 *zp = reinterpret_cast<const bf16 *>(smraw + st * L::STAGE + L::A_BYTES) +
-                             (tid / 8) * (L::PLANE / 2) + (tid & 7);
-            for (int j = 0; j < MT; ++j) bsum += __bfloat162float(zp[j * 8]);
-        }
+        const uint32_t sa = sbase + st * L::STAGE, sb = sa + L::A_BYTES;
         if (tid == WG_MMA_TID) {
             tc_fence_after();
 #pragma unroll
@@ -626,7 +634,20 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
             }
             mma_commit(&mma_done[st]);
         }
+        {  // bias gradient: thread (part, co) sums pixels part*PPX .., then co adds the parts in order
+            const int co = tid % CO, part = tid / CO;
+            const bf16 *zp = reinterpret_cast<const bf16 *>(smraw + st * L::STAGE + L::A_BYTES) +
+                             (co / 8) * (L::PLANE / 2) + (co & 7) + part * PPX * 8;
+            float ps = 0.f;
+#pragma unroll
+            for (int j = 0; j < PPX; ++j) ps += __bfloat162float(zp[j * 8]);
+            red[part * CO + co] = ps;
+        }
+        __syncthreads();
+        if (tid < CO)
+            for (int q = 0; q < PARTS; ++q) bsum += red[q * CO + tid];
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // nothing in flight when the block ends
     // every MMA this block issued has completed once `done` arrives
     if (tid == WG_MMA_TID) mma_commit(done);
     const bool fin = mbar_wait(done, 0, status);
