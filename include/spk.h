@@ -112,19 +112,23 @@ int64_t spk_num_frames(int T, int stride);
 int spk_reconstruct(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold,
                     void *out_frames);
 
-/* Same reconstruction with HOST buffers: copies the stream to device buffers owned by the
- * context (allocated on first use, grown as needed), reconstructs, copies the frames back
- * and waits.  host_stream: uint8 [T][pitch]; host_frames: [T_out][H][W] of out_dtype.
- * Page-locked host memory makes the copies asynchronous DMA.  Synchronous.
+/* Same reconstruction with HOST buffers: copies the stream to a device buffer owned by the
+ * context (allocated on first use, grown as needed), reconstructs and waits.
+ * host_stream: uint8 [T][pitch]; host_frames: [T_out][H][W] of out_dtype.  If host_frames
+ * is page-locked memory mapped into the device's address space (cudaHostAlloc, pinned torch
+ * tensors), the kernel writes the frames into it directly over the host link; otherwise
+ * they go to a context-owned device buffer and are copied back.  Page-locked host_stream
+ * makes its copy asynchronous DMA.  Synchronous.
  * Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM, SPK_ERR_TIMEOUT, SPK_ERR_INTERNAL. */
 int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W, int T,
                          float threshold, void *host_frames);
 
 /* Asynchronous spk_reconstruct_host: enqueues the host-to-device copy of the stream, the
- * reconstruction and the device-to-host copy of the frames, and returns.  Consecutive calls
- * alternate between two internal lanes (a stream and a pair of device buffers each, grown
- * on demand), so that one call's device-to-host copy overlaps the next call's input copy and
- * scan.  Work already enqueued on ctx's stream is ordered before the call.  host_stream and
+ * reconstruction into a device buffer and the device-to-host copy of the frames (always by a
+ * copy engine, which keeps the SMs free for the next call's scan), and returns.  Consecutive
+ * calls alternate between two internal lanes (a stream and a pair of device buffers each,
+ * grown on demand), so that one call's device-to-host copy overlaps the next call's input
+ * copy and scan.  Work already enqueued on ctx's stream is ordered before the call.  host_stream and
  * host_frames must stay untouched until spk_synchronize(ctx) returns; it waits for every
  * call and reports device errors.  Pinned host memory keeps the copies asynchronous.
  * Errors: as spk_reconstruct_host. */

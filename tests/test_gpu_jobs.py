@@ -210,3 +210,31 @@ def test_host_async_lanes_equal_sync(env):
         spk.spk_reconstruct_host(R.ctx, st, 33, 70, 2500, 1.0, ref)
         assert torch.equal(o, ref)
     R.close()
+
+
+def test_host_calls_pinned_and_pageable_equal_device(env):
+    """The synchronous host-buffer call writes the frames into page-locked output buffers
+    directly from the kernel and copies them into pageable ones, the asynchronous one always
+    copies; every way the frames equal the device-buffer reconstruction bit for bit (fp32
+    and fp16)."""
+    torch, pkg = env
+    from paper_2412_11639_gb300 import spk
+    w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=41, W=77, T=3100, seed=8)
+    st = spkgen.make_stream(w)[0]
+    for dtype, npdt in ((torch.float32, np.float32), (torch.float16, np.float16)):
+        R = pkg.Reconstructor(order=2, stride=w.stride, dtype=dtype)
+        want = R(torch.from_numpy(st).cuda(), w.H, w.W, w.T, 1.0)
+        R.synchronize()
+        want = want.cpu().numpy()
+        pinned_in = torch.from_numpy(st).pin_memory()
+        for pinned in (True, False):
+            for call in (spk.spk_reconstruct_host, spk.spk_reconstruct_host_async):
+                if pinned:
+                    out = torch.full((w.T_out, w.H, w.W), -1.0, dtype=dtype).pin_memory()
+                else:
+                    out = np.full((w.T_out, w.H, w.W), -1.0, dtype=npdt)
+                call(R.ctx, pinned_in if pinned else st, w.H, w.W, w.T, 1.0, out)
+                spk.spk_synchronize(R.ctx)
+                got = out.numpy() if pinned else out
+                assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (dtype, pinned, call.__name__)
+        R.close()
