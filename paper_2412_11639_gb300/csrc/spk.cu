@@ -1011,11 +1011,23 @@ int launch_tfp(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
     return SPK_OK;
 }
 
-// the n-order tree runs single whole streams only (one job per launch)
+// the n-order tree runs single whole streams only (one job per launch).  Its node arrays are
+// dynamically indexed and live in local memory; for n = 3 a warp touches 56 words of them (7
+// KB), which fit in L1 if the kernel asks for the smallest shared-memory carveout that holds
+// one block: then one block runs per SM and its local memory stays in L1 (bench stream 76 ->
+// 50 ms).  Deeper trees touch too much for that to pay (n = 5: 165 -> 187 ms) and keep the
+// default carveout.  (The n-order calls are synchronous and never captured in a graph.)
 template <typename OutT, bool SEG, int MAXJ>
 int launch_norder(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
-    if constexpr (MAXJ == 1) return launch<5, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
-    else return fail(ctx, SPK_ERR_ARG, "the n-order tree runs whole streams only");
+    if constexpr (MAXJ == 1) {
+        auto kern = spk_scan_kernel<5, OutT, SEG, 1, TT_DEFAULT>;
+        const int carve = prm.jobs[0].order_n == 3 ? 45 : static_cast<int>(cudaSharedmemCarveoutDefault);
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve) != cudaSuccess)
+            return fail(ctx, SPK_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(cudaGetLastError()));
+        return launch<5, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
+    } else {
+        return fail(ctx, SPK_ERR_ARG, "the n-order tree runs whole streams only");
+    }
 }
 
 template <int MAXJ, int TT>
