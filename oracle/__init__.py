@@ -40,6 +40,10 @@ def _load():
                                            c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p,
                                            c.c_void_p, c.c_void_p, c.c_void_p]
         lib.oracle_reconstruct.restype = c.c_int
+        lib.oracle_reconstruct2.argtypes = lib.oracle_reconstruct.argtypes + [c.c_int, c.c_int]
+        lib.oracle_reconstruct2.restype = c.c_int
+        lib.oracle_u8.argtypes = [c.c_int64, c.c_int64, c.c_int64]
+        lib.oracle_u8.restype = c.c_int
         lib.oracle_spike_times.argtypes = [c.c_void_p, c.c_int64, c.c_int, c.c_int64, c.c_void_p]
         lib.oracle_spike_times.restype = c.c_int
         lib.oracle_set_threads.argtypes = [c.c_int]
@@ -50,9 +54,13 @@ def _load():
         lib.oracle_tfi.argtypes = [c.c_void_p, c.c_int64, c.c_int64, c.c_int, c.c_double, c.c_int,
                                    c.c_void_p, c.c_int64, c.c_void_p]
         lib.oracle_tfi.restype = c.c_int
+        lib.oracle_tfi2.argtypes = lib.oracle_tfi.argtypes + [c.c_int, c.c_int]
+        lib.oracle_tfi2.restype = c.c_int
         lib.oracle_tfp.argtypes = [c.c_void_p, c.c_int64, c.c_int64, c.c_int, c.c_double, c.c_int,
                                    c.c_int, c.c_void_p, c.c_int64, c.c_void_p]
         lib.oracle_tfp.restype = c.c_int
+        lib.oracle_tfp2.argtypes = lib.oracle_tfp.argtypes + [c.c_int]
+        lib.oracle_tfp2.restype = c.c_int
         _lib = lib
     return _lib
 
@@ -107,11 +115,22 @@ class Result:
         return (self.seg_ts[a:b], self.seg_te[a:b], self.seg_n[a:b], self.seg_val[a:b])
 
 
+ZERO_HEAD, ZERO_TAIL = 1, 2   # frame edge policy bits
+
+
+def u8(theta: int, N: int, D: int) -> int:
+    """8-bit value of a sequence of N intervals over D steps: theta * N / D rounded half up,
+    clamped to 255 (theta integral)."""
+    return _load().oracle_u8(theta, N, D)
+
+
 def reconstruct(stream: np.ndarray, H: int, W: int, T: int, theta: float = 1.0, order: int = 1,
                 stride: int = 1, pixels=None, frames: bool = True,
-                segments: bool = False) -> Result:
+                segments: bool = False, edges: int = 0, u8: bool = False) -> Result:
     """Run the oracle on packed stream [T][pitch] for the given pixels (default: all).
-    order 1 = FSR, 2 = SSR, n > 2 = the general n-order tree (up to 32)."""
+    order 1 = FSR, 2 = SSR, n > 2 = the general n-order tree (up to 32).  edges: ZERO_HEAD
+    and/or ZERO_TAIL (frames up to the first / after the last spike read 0 instead of the
+    edge sequence's value); u8: frames hold the 8-bit values (theta integral)."""
     stream = np.ascontiguousarray(stream, dtype=np.uint8)
     if stream.ndim != 2 or stream.shape[0] < T:
         raise ValueError("stream must be [T][pitch]")
@@ -125,9 +144,9 @@ def reconstruct(stream: np.ndarray, H: int, W: int, T: int, theta: float = 1.0, 
     r.nseg = np.empty(npix, dtype=np.int32)
     lib = _load()
     fr = np.empty((T_out, npix), dtype=np.float64) if frames else None
-    rc = lib.oracle_reconstruct(stream.ctypes.data, pitch, P, T, theta, order, stride, _ptr(pix),
-                                npix, _ptr(fr), r.K.ctypes.data, r.nseg.ctypes.data,
-                                None, None, None, None, None)
+    rc = lib.oracle_reconstruct2(stream.ctypes.data, pitch, P, T, theta, order, stride, _ptr(pix),
+                                 npix, _ptr(fr), r.K.ctypes.data, r.nseg.ctypes.data,
+                                 None, None, None, None, None, edges, int(bool(u8)))
     if rc != 0:
         raise ValueError(f"oracle_reconstruct failed ({rc})")
     r.frames = fr
@@ -150,28 +169,29 @@ def reconstruct(stream: np.ndarray, H: int, W: int, T: int, theta: float = 1.0, 
 
 
 def tfi(stream: np.ndarray, H: int, W: int, T: int, theta: float = 1.0, stride: int = 1,
-        pixels=None) -> np.ndarray:
-    """TFI baseline (Sec. II): frames fp64 [T_out][npix]."""
+        pixels=None, edges: int = 0, u8: bool = False) -> np.ndarray:
+    """TFI baseline (Sec. II): frames fp64 [T_out][npix] (8-bit values with u8)."""
     stream = np.ascontiguousarray(stream, dtype=np.uint8)
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
     npix = H * W if pix is None else pix.shape[0]
     out = np.empty(((T + stride - 1) // stride, npix), dtype=np.float64)
-    rc = _load().oracle_tfi(stream.ctypes.data, stream.shape[1], H * W, T, theta, stride, _ptr(pix),
-                            npix, out.ctypes.data)
+    rc = _load().oracle_tfi2(stream.ctypes.data, stream.shape[1], H * W, T, theta, stride, _ptr(pix),
+                             npix, out.ctypes.data, edges, int(bool(u8)))
     if rc != 0:
         raise ValueError(f"oracle_tfi failed ({rc})")
     return out
 
 
 def tfp(stream: np.ndarray, H: int, W: int, T: int, window: int, theta: float = 1.0,
-        stride: int = 1, pixels=None) -> np.ndarray:
-    """TFP baseline (Sec. II) with a window of `window` steps: frames fp64 [T_out][npix]."""
+        stride: int = 1, pixels=None, u8: bool = False) -> np.ndarray:
+    """TFP baseline (Sec. II) with a window of `window` steps: frames fp64 [T_out][npix]
+    (8-bit values with u8)."""
     stream = np.ascontiguousarray(stream, dtype=np.uint8)
     pix = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
     npix = H * W if pix is None else pix.shape[0]
     out = np.empty(((T + stride - 1) // stride, npix), dtype=np.float64)
-    rc = _load().oracle_tfp(stream.ctypes.data, stream.shape[1], H * W, T, theta, stride, window,
-                            _ptr(pix), npix, out.ctypes.data)
+    rc = _load().oracle_tfp2(stream.ctypes.data, stream.shape[1], H * W, T, theta, stride, window,
+                             _ptr(pix), npix, out.ctypes.data, int(bool(u8)))
     if rc != 0:
         raise ValueError(f"oracle_tfp failed ({rc})")
     return out

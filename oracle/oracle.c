@@ -23,7 +23,8 @@
  *   6. frames: frame k samples t_k = k * stride and takes the value of the sequence
  *      covering t_k, a sequence of intervals i0..i1 covering the steps
  *      (s_{i0}, s_{i1+1}].  Steps up to s_1 take the first sequence's value, steps
- *      after s_K the last one's, and a pixel with fewer than two spikes reads 0.
+ *      after s_K the last one's (or 0 under the zero edge policies), and a pixel with
+ *      fewer than two spikes reads 0; 8-bit frames round theta * N / D half up (oracle_u8).
  *
  * Readings where the paper is silent (frame policy, cut position, hierarchy of the
  * two orders) are the ones listed in the design notes of this repository.
@@ -223,9 +224,25 @@ int oracle_segments_n(const int32_t *s, int K, int n, double theta, int32_t *t_s
     return nseg;
 }
 
-/* Step 6 for one pixel: frames[k * fstride] for k = 0 .. ceil(T/stride)-1. */
-void oracle_frames(int K, int nseg, const int32_t *t_start, const int32_t *t_end,
-                   const double *val, int T, int stride, double *frames, int64_t fstride) {
+/*
+ * 8-bit output (the paper's decoder writes 8-bit frames, Sec. III-C, and Eq. 4 carries the
+ * 8-bit scale 255): the value theta * N / D of a sequence of N intervals over D steps,
+ * rounded half up and clamped to 255, in exact integer arithmetic for an integral theta:
+ * floor((2 theta N + D) / (2 D)).
+ */
+int oracle_u8(int64_t theta, int64_t N, int64_t D) {
+    int64_t v = (2 * theta * N + D) / (2 * D);
+    return v > 255 ? 255 : (int)v;
+}
+
+/* Frame edge policy bits: frames up to the first spike read 0 instead of the first
+ * sequence's value, frames after the last spike read 0 instead of the last one's. */
+enum { ORACLE_ZERO_HEAD = 1, ORACLE_ZERO_TAIL = 2 };
+
+/* Step 6 for one pixel: frames[k * fstride] for k = 0 .. ceil(T/stride)-1, under the edge
+ * policy `edges`. */
+void oracle_frames_edges(int K, int nseg, const int32_t *t_start, const int32_t *t_end,
+                         const double *val, int T, int stride, int edges, double *frames, int64_t fstride) {
     int T_out = (T + stride - 1) / stride;
     int j = 0;
     for (int k = 0; k < T_out; ++k) {
@@ -234,15 +251,21 @@ void oracle_frames(int K, int nseg, const int32_t *t_start, const int32_t *t_end
         if (K < 2 || nseg == 0) {
             v = 0.0;
         } else if (t <= t_start[0]) {
-            v = val[0];                               /* before the first spike */
+            v = (edges & ORACLE_ZERO_HEAD) ? 0.0 : val[0];          /* up to the first spike */
         } else if (t > t_end[nseg - 1]) {
-            v = val[nseg - 1];                        /* after the last spike */
+            v = (edges & ORACLE_ZERO_TAIL) ? 0.0 : val[nseg - 1];   /* after the last spike */
         } else {
             while (!(t_start[j] < t && t <= t_end[j])) ++j;   /* covering sequence */
             v = val[j];
         }
         frames[(int64_t)k * fstride] = v;
     }
+}
+
+/* Step 6 with head fill and tail hold. */
+void oracle_frames(int K, int nseg, const int32_t *t_start, const int32_t *t_end,
+                   const double *val, int T, int stride, double *frames, int64_t fstride) {
+    oracle_frames_edges(K, nseg, t_start, t_end, val, T, stride, 0, frames, fstride);
 }
 
 /*
@@ -256,10 +279,28 @@ void oracle_frames(int K, int nseg, const int32_t *t_start, const int32_t *t_end
  *           from its slot size makes the call return -2.
  * Returns 0, -1 on bad arguments, -2 on a segment-slot mismatch.
  */
+int oracle_reconstruct2(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta,
+                        int order, int stride, const int64_t *pix, int64_t npix, double *frames,
+                        int32_t *K_out, int32_t *nseg_out, const int64_t *seg_off,
+                        int32_t *seg_ts, int32_t *seg_te, int32_t *seg_n, double *seg_val,
+                        int edges, int u8);
+
 int oracle_reconstruct(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta,
                        int order, int stride, const int64_t *pix, int64_t npix, double *frames,
                        int32_t *K_out, int32_t *nseg_out, const int64_t *seg_off,
                        int32_t *seg_ts, int32_t *seg_te, int32_t *seg_n, double *seg_val) {
+    return oracle_reconstruct2(stream, pitch, P, T, theta, order, stride, pix, npix, frames, K_out, nseg_out,
+                               seg_off, seg_ts, seg_te, seg_n, seg_val, 0, 0);
+}
+
+/* The same with a frame edge policy and, if u8, 8-bit frame values (oracle_u8 of each
+ * sequence, theta integral) instead of fp64 ones. */
+int oracle_reconstruct2(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta,
+                        int order, int stride, const int64_t *pix, int64_t npix, double *frames,
+                        int32_t *K_out, int32_t *nseg_out, const int64_t *seg_off,
+                        int32_t *seg_ts, int32_t *seg_te, int32_t *seg_n, double *seg_val,
+                        int edges, int u8) {
+    if (u8 && (theta != (double)(int64_t)theta || theta < 1)) return -1;
     if (P <= 0 || T <= 0 || pitch * 8 < P || stride <= 0 || order < 1 || order > 32) return -1;
     if (pix == NULL) npix = P;
     int err = 0;
@@ -296,7 +337,11 @@ int oracle_reconstruct(const uint8_t *stream, int64_t pitch, int64_t P, int T, d
                     memcpy(seg_val + o, vv, sizeof(double) * (size_t)ns);
                 }
             }
-            if (frames) oracle_frames(K, ns, ts, te, vv, T, stride, frames + i, npix);
+            if (frames) {
+                if (u8)  /* the frame values become the 8-bit ones of the same sequences */
+                    for (int q = 0; q < ns; ++q) vv[q] = (double)oracle_u8((int64_t)theta, nn[q], te[q] - ts[q]);
+                oracle_frames_edges(K, ns, ts, te, vv, T, stride, edges, frames + i, npix);
+            }
         }
         free(s);
         free(ts);
@@ -322,9 +367,19 @@ int oracle_reconstruct(const uint8_t *stream, int64_t pitch, int64_t P, int T, d
  *
  * frames [T_out][npix] fp64 as in oracle_reconstruct; pix == NULL means all pixels.
  */
+int oracle_tfi2(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta, int stride,
+                const int64_t *pix, int64_t npix, double *frames, int edges, int u8);
+
 int oracle_tfi(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta, int stride,
                const int64_t *pix, int64_t npix, double *frames) {
+    return oracle_tfi2(stream, pitch, P, T, theta, stride, pix, npix, frames, 0, 0);
+}
+
+/* TFI under a frame edge policy, fp64 or 8-bit (oracle_u8 with N = 1) values. */
+int oracle_tfi2(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta, int stride,
+                const int64_t *pix, int64_t npix, double *frames, int edges, int u8) {
     if (P <= 0 || T <= 0 || pitch * 8 < P || stride <= 0) return -1;
+    if (u8 && (theta != (double)(int64_t)theta || theta < 1)) return -1;
     if (pix == NULL) npix = P;
     int T_out = (T + stride - 1) / stride;
     int err = 0;
@@ -346,7 +401,10 @@ int oracle_tfi(const uint8_t *stream, int64_t pitch, int64_t P, int T, double th
                 double v = 0.0;
                 if (K >= 2) {
                     while (j < K - 2 && t > s[j + 1]) ++j;
-                    v = theta / (double)(s[j + 1] - s[j]);
+                    const int x = s[j + 1] - s[j];
+                    v = u8 ? (double)oracle_u8((int64_t)theta, 1, x) : theta / (double)x;
+                    if ((edges & ORACLE_ZERO_HEAD) && t <= s[0]) v = 0.0;
+                    if ((edges & ORACLE_ZERO_TAIL) && t > s[K - 1]) v = 0.0;
                 }
                 frames[(int64_t)k * npix + i] = v;
             }
@@ -356,9 +414,19 @@ int oracle_tfi(const uint8_t *stream, int64_t pitch, int64_t P, int T, double th
     return err;
 }
 
+int oracle_tfp2(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta, int stride, int L,
+                const int64_t *pix, int64_t npix, double *frames, int u8);
+
 int oracle_tfp(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta, int stride, int L,
                const int64_t *pix, int64_t npix, double *frames) {
+    return oracle_tfp2(stream, pitch, P, T, theta, stride, L, pix, npix, frames, 0);
+}
+
+/* TFP with fp64 or 8-bit values (oracle_u8 of the count over the window). */
+int oracle_tfp2(const uint8_t *stream, int64_t pitch, int64_t P, int T, double theta, int stride, int L,
+                const int64_t *pix, int64_t npix, double *frames, int u8) {
     if (P <= 0 || T <= 0 || pitch * 8 < P || stride <= 0 || L <= 0) return -1;
+    if (u8 && (theta != (double)(int64_t)theta || theta < 1)) return -1;
     if (pix == NULL) npix = P;
     int T_out = (T + stride - 1) / stride;
     int err = 0;
@@ -375,7 +443,7 @@ int oracle_tfp(const uint8_t *stream, int64_t pitch, int64_t P, int T, double th
             int n = 0;
             for (int64_t u = t - L + 1; u <= t; ++u)
                 if (u >= 0 && u < T && spike_bit(stream, pitch, (int)u, p)) ++n;
-            frames[(int64_t)k * npix + i] = theta * (double)n / (double)L;
+            frames[(int64_t)k * npix + i] = u8 ? (double)oracle_u8((int64_t)theta, n, L) : theta * (double)n / (double)L;
         }
     }
     return err;

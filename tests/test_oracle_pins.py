@@ -499,3 +499,67 @@ def test_constant_span_is_tfp_over_that_span():
         assert v == pytest.approx(n / D, rel=1e-15)
         checked += 1
     assert checked > 40
+
+
+# ------------------------------------------------------------ 8-bit frames, edge policy ----
+def test_u8_is_round_half_up_of_the_exact_ratio():
+    """The 8-bit value of a sequence (the decoder's 8-bit output, Sec. III-C; Eq. 4 with
+    its 8-bit scale): theta * N / D rounded half up and clamped to 255, checked against
+    exact rationals, ties included."""
+    from fractions import Fraction
+    rng = np.random.default_rng(17)
+    cases = [(255, 1, 2), (255, 3, 7), (1, 1, 2), (1, 3, 2), (2, 5, 4), (255, 20, 2), (7, 9, 14)]
+    cases += [(int(t), int(n), int(d)) for t, n, d in zip(rng.choice([1, 2, 7, 255, 1000], 3000),
+                                                          rng.integers(1, 5000, 3000), rng.integers(1, 20000, 3000))]
+    for theta, N, D in cases:
+        want = min(255, int((Fraction(theta * N, D) + Fraction(1, 2)) // 1))
+        assert oracle.u8(theta, N, D) == want, (theta, N, D)
+    assert oracle.u8(1, 1, 2) == 1 and oracle.u8(1, 1, 3) == 0 and oracle.u8(3, 1, 2) == 2   # ties round up
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_u8_frames_are_the_covering_sequences_u8(order):
+    w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=6, W=30, T=1500)
+    st, _ = spkgen.make_stream(w)
+    for theta in (255, 1):
+        r = oracle.reconstruct(st, w.H, w.W, w.T, float(theta), order, w.stride, segments=True)
+        u = oracle.reconstruct(st, w.H, w.W, w.T, float(theta), order, w.stride, u8=True)
+        f, g = r.frames, u.frames
+        assert np.all(g == np.round(g)) and g.min() >= 0 and g.max() <= 255
+        ok = f <= 255.5
+        assert np.all(np.abs(g[ok] - f[ok]) <= 0.5 + 1e-9)        # the nearest integer
+        assert np.all(g[~ok] == 255)
+        for p in range(w.P):                                    # and exactly the sequence's u8
+            ts, te, n, _ = r.segments(p)
+            vals = {oracle.u8(theta, int(a), int(b) - int(c)) for a, b, c in zip(n, te, ts)}
+            assert set(np.unique(g[:, p])) <= vals | {0.0}
+
+
+@pytest.mark.parametrize("order", [1, 2, 4])
+def test_edge_policies_zero_only_the_edges(order):
+    """ZERO_HEAD makes the frames up to the first spike 0, ZERO_TAIL those after the last
+    spike; every other frame keeps its value (the frame policy of A4, with the edges off)."""
+    w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=5, W=40, T=1200)
+    st, _ = spkgen.make_stream(w)
+    bits = np.zeros((w.T, w.P), dtype=np.uint8)
+    bits[100:900:7, :] = 1                         # every pixel: spikes from 100 to 897 only
+    st2 = spkgen.pack(bits, w.H, w.W)
+    for s in (st, st2):
+        base = oracle.reconstruct(s, w.H, w.W, w.T, 1.0, order, 3).frames
+        tk = np.arange(base.shape[0])[:, None] * 3
+        s1 = np.array([oracle.spike_times(s, w.T, p)[0] for p in range(w.P)])[None, :]
+        sK = np.array([oracle.spike_times(s, w.T, p)[-1] for p in range(w.P)])[None, :]
+        for edges in (oracle.ZERO_HEAD, oracle.ZERO_TAIL, oracle.ZERO_HEAD | oracle.ZERO_TAIL):
+            f = oracle.reconstruct(s, w.H, w.W, w.T, 1.0, order, 3, edges=edges).frames
+            zero = np.zeros_like(base, dtype=bool)
+            if edges & oracle.ZERO_HEAD:
+                zero |= tk <= s1
+            if edges & oracle.ZERO_TAIL:
+                zero |= tk > sK
+            assert np.all(f[zero] == 0) and np.array_equal(f[~zero], base[~zero])
+        if s is st2:
+            assert (tk <= s1).any() and (tk > sK).any()
+        t0 = oracle.tfi(s, w.H, w.W, w.T, 1.0, 3)
+        t1 = oracle.tfi(s, w.H, w.W, w.T, 1.0, 3, edges=oracle.ZERO_HEAD | oracle.ZERO_TAIL)
+        zero = (tk <= s1) | (tk > sK)
+        assert np.all(t1[zero] == 0) and np.array_equal(t1[~zero], t0[~zero])
