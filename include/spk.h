@@ -22,8 +22,9 @@
  *    Padding bits and bytes are ignored.
  *  - Frame k (k = 0 .. T_out-1, T_out = spk_num_frames(T, stride)) samples t_k = k*stride
  *    and holds the value of the stable sequence covering t_k.  Steps up to the first spike
- *    take the first sequence's value, steps after the last spike the last one's, and a
- *    pixel with fewer than two spikes reads 0.  Frame layout: [T_out][H][W], row-major.
+ *    take the first sequence's value, steps after the last spike the last one's (or 0
+ *    under spk_config.edges), and a pixel with fewer than two spikes reads 0.  Frame
+ *    layout: [T_out][H][W], row-major, 4, 2 or 1 bytes a value (spk_config.out_dtype).
  *  - Device pointers must be CUDA device (or managed) memory and 16-byte aligned.
  *  - Calls are asynchronous on the context's stream unless stated; spk_synchronize()
  *    waits and reports device-side failures.  A context is not thread-safe: use one per
@@ -50,7 +51,17 @@ enum spk_status {
     SPK_ERR_INTERNAL = -5  /* a device-side consistency check failed */
 };
 
-enum spk_dtype { SPK_F32 = 0, SPK_F16 = 1 };
+/* Frame value types.  SPK_U8 gives the 8-bit frames of a decoder (Sec. III-C with the 8-bit
+ * scale of Eq. 4): threshold * N / D rounded half up and clamped to 255, computed exactly
+ * in integers; it needs an integral threshold in 1 .. 65535. */
+enum spk_dtype { SPK_F32 = 0, SPK_F16 = 1, SPK_U8 = 2 };
+
+/* Frame edge policy bits (spk_config.edges).  The paper leaves the frames before the first
+ * spike and after the last one open; by default they hold the first and the last stable
+ * sequence's value.  SPK_ZERO_HEAD: frames at or before the first spike read 0.
+ * SPK_ZERO_TAIL: frames after the last spike read 0.  TFP has no edges and ignores them;
+ * spk_segments reports spans, not frames, and ignores them too. */
+enum spk_edges { SPK_ZERO_HEAD = 1, SPK_ZERO_TAIL = 2 };
 
 /* Reconstruction methods.  FSR and SSR are the paper's (Sec. III-B); TFI and TFP are the
  * physical-model baselines it compares them with (Sec. II, Tables II-III):
@@ -74,12 +85,13 @@ enum spk_method { SPK_FSR = 1, SPK_SSR = 2, SPK_TFI = 3, SPK_TFP = 4, SPK_NORDER
 typedef struct spk_config {
     int method;         /* SPK_FSR, SPK_SSR, SPK_TFI, SPK_TFP or SPK_NORDER */
     int frame_stride;   /* >= 1: frame k samples step k * frame_stride */
-    int out_dtype;      /* SPK_F32 or SPK_F16 (fp16 is the round-to-nearest-even of the
-                           fp32 value) */
+    int out_dtype;      /* SPK_F32, SPK_F16 (the round-to-nearest-even of the fp32 value) or
+                           SPK_U8 (integral threshold, see spk_dtype) */
     int device;         /* CUDA device ordinal */
     void *stream;       /* cudaStream_t to launch on; NULL = the legacy default stream */
     int tfp_window;     /* SPK_TFP only: window L in steps, 1..64 (the paper uses 32, 64) */
     int stability_order; /* SPK_NORDER only: levels n of the stability tree, 3..5 */
+    int edges;          /* 0 or SPK_ZERO_HEAD | SPK_ZERO_TAIL (frame edge policy) */
 } spk_config;
 
 typedef struct spk_ctx spk_ctx;
@@ -105,7 +117,8 @@ int64_t spk_num_frames(int T, int stride);
 /* Reconstructs every frame of one stream (Sec. III-B, Eq. 4).
  *   stream      device, uint8 [T][spk_pitch(H, W)], read only, owned by the caller
  *   H, W, T     sensor rows, columns, steps (> 0)
- *   threshold   finite, > 0: the scale of Eq. 4 (255 for 8-bit images, 1 for rates)
+ *   threshold   finite, > 0: the scale of Eq. 4 (255 for 8-bit images, 1 for rates);
+ *               integral, 1 .. 65535, for SPK_U8 frames
  *   out_frames  device, [T_out][H][W] of the context's out_dtype, written completely,
  *               owned by the caller; must not overlap `stream`
  * Asynchronous on the context's stream.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA. */

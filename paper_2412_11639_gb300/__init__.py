@@ -8,13 +8,14 @@ from __future__ import annotations
 
 from . import spk
 from .build import build
-from .spk import (SPK_F16, SPK_F32, SpkError, spk_create, spk_destroy, spk_launch_count,
+from .spk import (SPK_F16, SPK_F32, SPK_U8, SPK_ZERO_HEAD, SPK_ZERO_TAIL, SpkError, spk_create, spk_destroy, spk_launch_count,
                   spk_last_error, spk_num_frames, spk_pitch, spk_reconstruct,
                   spk_reconstruct_host, spk_reconstruct_host_async, spk_run, spk_segments,
                   spk_stream_close, spk_stream_open, spk_stream_ready, spk_stream_steps,
                   spk_synchronize)
 
-__all__ = ["spk", "build", "Reconstructor", "SpkError", "SPK_F32", "SPK_F16", "spk_create",
+__all__ = ["spk", "build", "Reconstructor", "SpkError", "SPK_F32", "SPK_F16", "SPK_U8", "SPK_ZERO_HEAD",
+           "SPK_ZERO_TAIL", "spk_create",
            "spk_destroy", "spk_pitch", "spk_num_frames", "spk_reconstruct",
            "spk_reconstruct_host", "spk_reconstruct_host_async", "spk_segments", "spk_synchronize", "spk_last_error",
            "spk_launch_count", "spk_run", "spk_stream_open", "spk_stream_close",
@@ -26,22 +27,25 @@ class Reconstructor:
 
     order (the method): 1 = FSR, 2 = SSR, 3 = TFI, 4 = TFP (window tfp_window steps),
     5 = the general n-order stability tree with stability_order levels (3..5);
-    frame k samples step k * stride; dtype torch.float32 or torch.float16.  Device memory
+    frame k samples step k * stride; dtype torch.float32, torch.float16 or torch.uint8 (8-bit
+    frames: threshold * N / D rounded half up, integral thresholds); edges 0 or SPK_ZERO_HEAD |
+    SPK_ZERO_TAIL (frames up to the first / after the last spike read 0).  Device memory
     comes from torch; the reconstruction runs in libspk.
     """
 
     def __init__(self, order: int = 2, stride: int = 1, dtype=None, device: int = 0,
-                 stream=None, tfp_window: int = 32, stability_order: int = 3):
+                 stream=None, tfp_window: int = 32, stability_order: int = 3, edges: int = 0):
         import torch
         self.torch = torch
         dtype = dtype or torch.float32
-        if dtype not in (torch.float32, torch.float16):
-            raise ValueError("dtype must be torch.float32 or torch.float16")
+        kinds = {torch.float32: SPK_F32, torch.float16: SPK_F16, torch.uint8: SPK_U8}
+        if dtype not in kinds:
+            raise ValueError("dtype must be torch.float32, torch.float16 or torch.uint8")
         self.dtype = dtype
         self.order, self.stride, self.device = order, stride, device
         self.stream = stream or torch.cuda.current_stream(device)
-        self.ctx = spk_create(order, stride, SPK_F16 if dtype == torch.float16 else SPK_F32,
-                              device, self.stream.cuda_stream, tfp_window, stability_order)
+        self.ctx = spk_create(order, stride, kinds[dtype], device, self.stream.cuda_stream, tfp_window,
+                              stability_order, edges)
 
     def close(self):
         if self.ctx is not None:

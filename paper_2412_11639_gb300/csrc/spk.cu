@@ -91,6 +91,7 @@ struct Job {
     float theta;    // threshold of Eq. 4
     int window;     // TFP window in steps
     int order_n;    // levels of the n-order tree (method SPK_NORDER)
+    int edges;      // frame edge policy (EDGE_ZERO_HEAD | EDGE_ZERO_TAIL)
     int flags;      // JOB_FIRST | JOB_LAST
     int block0;     // first block of this job in the flat grid
 };
@@ -193,6 +194,26 @@ __device__ __forceinline__ float seq_value(float theta, int n, int d) {
     return __fdiv_rn(__fmul_rn(theta, static_cast<float>(n)), static_cast<float>(d));
 }
 
+// 8-bit output (the decoder's 8-bit frames, Sec. III-C, with the 8-bit scale of Eq. 4):
+// theta * N / D rounded half up and clamped to 255, exactly, in integers (theta integral).
+__device__ __forceinline__ int seq_u8(int theta, int n, int d) {
+    const long long v = (2LL * theta * n + d) / (2LL * d);
+    return v > 255 ? 255 : static_cast<int>(v);
+}
+// a span's value as a record stores it: the fp32 bits, or the 8-bit value for uint8_t frames
+template <typename OutT>
+__device__ __forceinline__ int value_bits(float theta, int n, int d) {
+    if constexpr (std::is_same_v<OutT, uint8_t>) return seq_u8(static_cast<int>(theta), n, d);
+    else return __float_as_int(seq_value(theta, n, d));
+}
+template <typename OutT>
+__device__ __forceinline__ OutT from_bits(int b) {
+    if constexpr (std::is_same_v<OutT, uint8_t>) return static_cast<uint8_t>(b);
+    else return to_out<OutT>(__int_as_float(b));
+}
+// frame edge policy bits (spk_config.edges)
+constexpr int EDGE_ZERO_HEAD = SPK_ZERO_HEAD, EDGE_ZERO_TAIL = SPK_ZERO_TAIL;
+
 // --------------------------------------------------------------------- sinks ----
 // Cuts of one lane, in time order, in a per-lane shared-memory ring.  Stable spans run
 // between consecutive cuts, so span j has N = i_j - i_{j-1} intervals over
@@ -224,7 +245,8 @@ struct FrameSink {
     int kf;          // frames < kf are covered by converted records
     int bad;         // set if a flush found no record for a frame (never expected)
     int ct, ci;      // the last converted cut (the first spike and -1 before the first)
-    float cv;        // value of the last converted span (0 before the first)
+    int cvb;         // value bits (value_bits) of the last converted span (0 before the first)
+    int zero_tail;   // frames after the last spike read 0 (edge policy)
     int cur_ke;      // cursor: the record at head covers frames up to cur_ke, value cur_o
     OutT cur_o;
 
@@ -235,7 +257,7 @@ struct FrameSink {
     __device__ __forceinline__ void load() {
         const int s = slot(head);
         cur_ke = rt[s];
-        cur_o = to_out<OutT>(__int_as_float(ri[s]));
+        cur_o = from_bits<OutT>(ri[s]);
     }
     // A candidate that arrived one place early is swapped in front of its predecessor
     // (converted records are final and never move).
@@ -263,13 +285,13 @@ struct FrameSink {
                 ke = T_out - 1;
             } else {
                 const int i = ri[s];
-                cv = seq_value(theta, i - ci, t - ct);
+                cvb = value_bits<OutT>(theta, i - ci, t - ct);
                 ct = t;
                 ci = i;
                 ke = frame_of(t);
             }
             rt[s] = ke;
-            ri[s] = __float_as_int(cv);
+            ri[s] = (t == TAIL && zero_tail) ? 0 : cvb;
             kf = max(kf, ke + 1);
         }
     }
@@ -279,6 +301,18 @@ struct FrameSink {
         int R = tail;
         if (R > conv && rt[slot(R - 1)] > frontier) --R;
         convert(R);
+    }
+    // Edge policy: frames up to the first spike t0 read 0.  At the first spike the ring is
+    // empty; a converted record (last frame frame_of(t0), value 0) goes ahead of the first
+    // span, which then covers only the frames after t0.
+    __device__ __forceinline__ void zero_head(int t0) {
+        const int s = slot(tail);
+        const int ke = frame_of(t0);
+        rt[s] = ke;
+        ri[s] = 0;
+        ++tail;
+        sorted = conv = tail;
+        kf = max(kf, ke + 1);
     }
     __device__ __forceinline__ void drain_one() {  // ring full: write the oldest record alone
         sort_new();
@@ -535,8 +569,9 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         fs.head = fs.tail = fs.sorted = fs.conv = fs.W = fs.kf = fs.bad = 0;
         fs.ct = fs.cur_ke = 0;
         fs.ci = -1;
-        fs.cv = 0.f;
-        fs.cur_o = to_out<OutT>(0.f);
+        fs.cvb = 0;
+        fs.zero_tail = (job.edges & EDGE_ZERO_TAIL) != 0;
+        fs.cur_o = from_bits<OutT>(0);
         if constexpr (ORDER != 5)
             if (!(job.flags & JOB_FIRST) && valid) carry_load(job.carry, job.P, p, sc, fs);
     }
@@ -564,8 +599,12 @@ __global__ void __launch_bounds__(NTHREADS, 3)
             if (sc.last_t < 0 && w) {  // the stream's first spike opens the first sequence
                 const int t0 = base + __ffs(w) - 1;
                 sc.first_spike(t0);
-                if constexpr (SEGMENTS) ss.ct = t0;  // the first span starts here
-                else fs.ct = t0;
+                if constexpr (SEGMENTS) {
+                    ss.ct = t0;  // the first span starts here
+                } else {
+                    fs.ct = t0;
+                    if (job.edges & EDGE_ZERO_HEAD) fs.zero_head(t0);
+                }
                 w &= w - 1;
             }
             if (w == 0xffffffffu && sc.absorb_ones(base)) w = 0;  // steady run of 1-intervals
@@ -712,7 +751,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) spk_tfp_kernel(const __grid_const
                 int cnt = __popc(w & upto & ~((1u << (lo > 0 ? lo : 0)) - 1u));
                 if (lo < 0) cnt += __popcll(hist >> (64 + lo));  // the -lo steps before this word
                 if (valid) col[static_cast<int64_t>(k) * job.P] =
-                    to_out<OutT>(__fdiv_rn(__fmul_rn(job.theta, static_cast<float>(cnt)), static_cast<float>(L)));
+                    from_bits<OutT>(value_bits<OutT>(job.theta, cnt, L));
             }
             h2 = h1;
             h1 = w;
@@ -953,6 +992,22 @@ int64_t pitch_of(int H, int W) {
     return ((P + 7) / 8 + 15) / 16 * 16;
 }
 
+// bytes per frame value of an output type
+size_t out_esz(int dtype) { return dtype == SPK_F16 ? 2 : dtype == SPK_U8 ? 1 : 4; }
+
+// spk_config fields beyond the method: frame stride, output type, edge policy
+const char *bad_output_cfg(const spk_config *cfg) {
+    if (cfg->frame_stride < 1) return "frame_stride must be >= 1";
+    if (cfg->out_dtype != SPK_F32 && cfg->out_dtype != SPK_F16 && cfg->out_dtype != SPK_U8) return "bad out_dtype";
+    if (cfg->edges < 0 || cfg->edges > (SPK_ZERO_HEAD | SPK_ZERO_TAIL)) return "bad edges";
+    return nullptr;
+}
+
+// 8-bit frames round theta * N / D in integers: theta must be integral, 1 .. 65535
+bool u8_threshold_ok(float threshold) {
+    return threshold >= 1.f && threshold <= 65535.f && threshold == std::floor(threshold);
+}
+
 // common argument checks of the stream-consuming calls
 int check_stream_args(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold) {
     if (!ctx) return SPK_ERR_ARG;
@@ -962,6 +1017,8 @@ int check_stream_args(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, 
         return fail(ctx, SPK_ERR_ARG, "H*W too large");
     if (!std::isfinite(threshold) || !(threshold > 0.f))
         return fail(ctx, SPK_ERR_ARG, "threshold must be finite and > 0");
+    if (ctx->cfg.out_dtype == SPK_U8 && !u8_threshold_ok(threshold))
+        return fail(ctx, SPK_ERR_ARG, "8-bit frames need an integral threshold in 1 .. 65535");
     if (reinterpret_cast<uintptr_t>(stream) % 16) return fail(ctx, SPK_ERR_ARG, "stream is not 16-byte aligned");
     if (T > (1 << 30)) return fail(ctx, SPK_ERR_ARG, "T too large");
     return SPK_OK;
@@ -1040,12 +1097,25 @@ int dispatch_tile(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
                         : launch<2, float, false, MAXJ, TT>(ctx, prm, nblocks);
 }
 
-// FSR / SSR frames kernels come in three time tiles (the autotuner's choice); TFI, TFP
-// and the verification kernel in the default tile only
+// 8-bit frames: every method in the default tile
+template <int MAXJ>
+int dispatch_u8(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
+    switch (ctx->cfg.method) {
+        case SPK_FSR: return launch<1, uint8_t, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+        case SPK_TFI: return launch<3, uint8_t, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+        case SPK_TFP: return launch_tfp<uint8_t, MAXJ>(ctx, prm, nblocks);
+        case SPK_NORDER: return launch_norder<uint8_t, false>(ctx, prm, nblocks);
+        default: return launch<2, uint8_t, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+    }
+}
+
+// FSR / SSR frames kernels come in three time tiles (the autotuner's choice); TFI, TFP,
+// 8-bit frames and the verification kernel in the default tile only
 template <int MAXJ>
 int dispatch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks, bool segments, int tile) {
     const int m = ctx->cfg.method;
     const bool f16 = ctx->cfg.out_dtype == SPK_F16;
+    if (!segments && ctx->cfg.out_dtype == SPK_U8) return dispatch_u8(ctx, prm, nblocks);
     if (segments)
         return m == SPK_FSR      ? launch<1, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
              : m == SPK_TFI      ? launch<3, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
@@ -1063,10 +1133,12 @@ int dispatch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks, bool segments, i
     return dispatch_tile<MAXJ, 64>(ctx, prm, nblocks);
 }
 
-// the tile a call will use: the context's for FSR / SSR, the default for the others
+// the tile a call will use: the context's for FSR / SSR frames of 4 or 2 bytes, the
+// default for the others
 int tile_of(const spk_ctx *ctx, bool segments) {
     const int m = ctx->cfg.method;
-    return (segments || m == SPK_TFI || m == SPK_TFP || m == SPK_NORDER) ? TT_DEFAULT : ctx->tile;
+    return (segments || m == SPK_TFI || m == SPK_TFP || m == SPK_NORDER || ctx->cfg.out_dtype == SPK_U8)
+               ? TT_DEFAULT : ctx->tile;
 }
 
 bool valid_method(const spk_config *cfg) {
@@ -1102,6 +1174,7 @@ int fill_job(spk_ctx *ctx, CUtensorMap *map, Job *job, const uint8_t *stream, in
     job->theta = threshold;
     job->window = ctx->cfg.tfp_window;
     job->order_n = ctx->cfg.stability_order;
+    job->edges = ctx->cfg.edges;
     job->flags = flags;
     job->block0 = block0;
     return static_cast<int>((P + BLOCK_PIX - 1) / BLOCK_PIX);
@@ -1185,8 +1258,7 @@ int spk_create(spk_ctx **out, const spk_config *cfg) {
     *out = nullptr;
     if (!cfg) return fail(nullptr, SPK_ERR_ARG, "cfg is NULL");
     if (!valid_method(cfg)) return fail(nullptr, SPK_ERR_ARG, "method must be 1..5 (TFP: tfp_window 1..64; NORDER: stability_order 3..5)");
-    if (cfg->frame_stride < 1) return fail(nullptr, SPK_ERR_ARG, "frame_stride must be >= 1");
-    if (cfg->out_dtype != SPK_F32 && cfg->out_dtype != SPK_F16) return fail(nullptr, SPK_ERR_ARG, "bad out_dtype");
+    if (const char *why = bad_output_cfg(cfg)) return fail(nullptr, SPK_ERR_ARG, "%s", why);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
         cudaGetLastError();
@@ -1246,7 +1318,7 @@ int spk_reconstruct(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, fl
     if (reinterpret_cast<uintptr_t>(out_frames) % 16) return fail(ctx, SPK_ERR_ARG, "out_frames is not 16-byte aligned");
     const int64_t P = static_cast<int64_t>(H) * W;
     const int64_t T_out = spk_num_frames(T, ctx->cfg.frame_stride);
-    const size_t esz = ctx->cfg.out_dtype == SPK_F16 ? 2 : 4;
+    const size_t esz = out_esz(ctx->cfg.out_dtype);
     const size_t out_bytes = static_cast<size_t>(T_out) * static_cast<size_t>(P) * esz;
     const size_t in_bytes = static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W));
     if (overlaps(stream, in_bytes, out_frames, out_bytes)) return fail(ctx, SPK_ERR_ARG, "out_frames overlaps stream");
@@ -1353,7 +1425,7 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
     if (!ctx) return SPK_ERR_ARG;
     ctx->msg[0] = 0;
     if (njobs < 0 || (njobs > 0 && !jobs)) return fail(ctx, SPK_ERR_ARG, "bad job list");
-    const size_t esz = ctx->cfg.out_dtype == SPK_F16 ? 2 : 4;
+    const size_t esz = out_esz(ctx->cfg.out_dtype);
     for (int k = 0; k < njobs; ++k) {  // validate everything before any launch
         const spk_job &jb = jobs[k];
         int rc = check_stream_args(ctx, jb.stream, jb.H, jb.W, jb.n, jb.threshold);
@@ -1520,7 +1592,7 @@ int spk_reconstruct_host(spk_ctx *ctx, const uint8_t *host_stream, int H, int W,
     if (!host_frames) return fail(ctx, SPK_ERR_ARG, "host_frames is NULL");
     const int64_t P = static_cast<int64_t>(H) * W;
     const int64_t T_out = spk_num_frames(T, ctx->cfg.frame_stride);
-    const size_t esz = ctx->cfg.out_dtype == SPK_F16 ? 2 : 4;
+    const size_t esz = out_esz(ctx->cfg.out_dtype);
     const size_t out_bytes = static_cast<size_t>(T_out) * static_cast<size_t>(P) * esz;
     const size_t in_bytes = static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W));
     cudaSetDevice(ctx->cfg.device);
@@ -1578,7 +1650,7 @@ int spk_reconstruct_host_async(spk_ctx *ctx, const uint8_t *host_stream, int H, 
     if (!host_frames) return fail(ctx, SPK_ERR_ARG, "host_frames is NULL");
     const int64_t P = static_cast<int64_t>(H) * W;
     const int64_t T_out = spk_num_frames(T, ctx->cfg.frame_stride);
-    const size_t esz = ctx->cfg.out_dtype == SPK_F16 ? 2 : 4;
+    const size_t esz = out_esz(ctx->cfg.out_dtype);
     const size_t out_bytes = static_cast<size_t>(T_out) * static_cast<size_t>(P) * esz;
     const size_t in_bytes = static_cast<size_t>(T) * static_cast<size_t>(pitch_of(H, W));
     cudaSetDevice(ctx->cfg.device);
@@ -1653,16 +1725,17 @@ extern "C" int spk_reconstruct_host_noalloc(const spk_config *cfg, const uint8_t
                                             int T, float threshold, void *host_frames) {
     if (!cfg) return fail(nullptr, SPK_ERR_ARG, "cfg is NULL");
     if (!valid_method(cfg)) return fail(nullptr, SPK_ERR_ARG, "method must be 1..5 (TFP: tfp_window 1..64; NORDER: stability_order 3..5)");
-    if (cfg->frame_stride < 1) return fail(nullptr, SPK_ERR_ARG, "frame_stride must be >= 1");
-    if (cfg->out_dtype != SPK_F32 && cfg->out_dtype != SPK_F16) return fail(nullptr, SPK_ERR_ARG, "bad out_dtype");
+    if (const char *why = bad_output_cfg(cfg)) return fail(nullptr, SPK_ERR_ARG, "%s", why);
     if (cfg->device < 0 || cfg->device >= NOALLOC_MAX_DEVICES) return fail(nullptr, SPK_ERR_ARG, "bad device ordinal");
     if (!host_stream || !host_frames) return fail(nullptr, SPK_ERR_ARG, "host_stream or host_frames is NULL");
     if (H <= 0 || W <= 0 || T <= 0) return fail(nullptr, SPK_ERR_ARG, "H, W, T must be > 0 (got %d, %d, %d)", H, W, T);
     if (!std::isfinite(threshold) || !(threshold > 0.f))
         return fail(nullptr, SPK_ERR_ARG, "threshold must be finite and > 0");
+    if (cfg->out_dtype == SPK_U8 && !u8_threshold_ok(threshold))
+        return fail(nullptr, SPK_ERR_ARG, "8-bit frames need an integral threshold in 1 .. 65535");
     const int64_t P = static_cast<int64_t>(H) * W;
     const int64_t T_out = spk_num_frames(T, cfg->frame_stride);
-    const size_t esz = cfg->out_dtype == SPK_F16 ? 2 : 4;
+    const size_t esz = out_esz(cfg->out_dtype);
     // the n-order tree also needs its pending-cut rings: 2 x NORDER_CAP0 ints per pixel at first
     const double ring_d = cfg->method == SPK_NORDER ? 2.0 * NORDER_CAP0 * sizeof(int) * static_cast<double>(P) : 0.0;
     const double need_d = static_cast<double>(NOALLOC_STATUS_BYTES) +

@@ -12,7 +12,8 @@ import os
 from .build import LIB
 
 SPK_OK, SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM, SPK_ERR_TIMEOUT, SPK_ERR_INTERNAL = 0, -1, -2, -3, -4, -5
-SPK_F32, SPK_F16 = 0, 1
+SPK_F32, SPK_F16, SPK_U8 = 0, 1, 2
+SPK_ZERO_HEAD, SPK_ZERO_TAIL = 1, 2  # frame edge policy bits
 SPK_FSR, SPK_SSR, SPK_TFI, SPK_TFP, SPK_NORDER = 1, 2, 3, 4, 5
 
 _c = ctypes
@@ -37,7 +38,7 @@ class SpkError(RuntimeError):
 class spk_config(ctypes.Structure):
     _fields_ = [("method", _c.c_int), ("frame_stride", _c.c_int), ("out_dtype", _c.c_int),
                 ("device", _c.c_int), ("stream", _c.c_void_p), ("tfp_window", _c.c_int),
-                ("stability_order", _c.c_int)]
+                ("stability_order", _c.c_int), ("edges", _c.c_int)]
 
 
 class spk_job(ctypes.Structure):
@@ -151,14 +152,19 @@ def _check(ctx, rc):
 _CTX_FRAMES = {}  # context handle -> (frame_stride, bytes per output value), for host-buffer checks
 
 
+def _esz(out_dtype: int) -> int:
+    """Bytes per frame value of an output type."""
+    return 2 if out_dtype == SPK_F16 else 1 if out_dtype == SPK_U8 else 4
+
+
 def spk_create(method: int = SPK_SSR, frame_stride: int = 1, out_dtype: int = SPK_F32, device: int = 0,
-               stream: int | None = None, tfp_window: int = 32, stability_order: int = 3):
+               stream: int | None = None, tfp_window: int = 32, stability_order: int = 3, edges: int = 0):
     lib = load()
-    cfg = spk_config(method, frame_stride, out_dtype, device, stream, tfp_window, stability_order)
+    cfg = spk_config(method, frame_stride, out_dtype, device, stream, tfp_window, stability_order, edges)
     ctx = _c.c_void_p()
     rc = lib.spk_create(_c.byref(ctx), _c.byref(cfg))
     _check(None, rc)
-    _CTX_FRAMES[ctx.value] = (frame_stride, 2 if out_dtype == SPK_F16 else 4)
+    _CTX_FRAMES[ctx.value] = (frame_stride, _esz(out_dtype))
     return ctx
 
 
@@ -242,13 +248,13 @@ def spk_selftest_wait(ctx, limit_cycles: int):
 def spk_reconstruct_host_noalloc(host_stream, H, W, T, threshold, host_frames, method: int = SPK_SSR,
                                  frame_stride: int = 1, out_dtype: int = SPK_F32, device: int = 0,
                                  stream: int | None = None, tfp_window: int = 32,
-                                 stability_order: int = 3):
+                                 stability_order: int = 3, edges: int = 0):
     """Host-buffer reconstruction staged in the library's fixed device array (no allocation).
     method: 1 FSR, 2 SSR, 3 TFI, 4 TFP (window tfp_window), 5 the n-order tree
     (stability_order levels, 3..5).  Raises ValueError, before any device work, if a buffer is
     strided or smaller than the call reads or writes."""
-    _check_host_buffers(host_stream, host_frames, H, W, T, frame_stride, 2 if out_dtype == SPK_F16 else 4)
-    cfg = spk_config(method, frame_stride, out_dtype, device, stream, tfp_window, stability_order)
+    _check_host_buffers(host_stream, host_frames, H, W, T, frame_stride, _esz(out_dtype))
+    cfg = spk_config(method, frame_stride, out_dtype, device, stream, tfp_window, stability_order, edges)
     rc = load().spk_reconstruct_host_noalloc(_c.byref(cfg), _addr(host_stream), H, W, T, threshold,
                                              _addr(host_frames))
     return _check(None, rc)

@@ -50,7 +50,9 @@ def test_create_rejects_bad_config(lib):
     for cfg in (spk.spk_config(6, 1, 0, 0, None, 32, 3), spk.spk_config(0, 1, 0, 0, None, 32, 3),
                 spk.spk_config(2, 0, 0, 0, None, 32, 3), spk.spk_config(1, 1, 7, 0, None, 32, 3),
                 spk.spk_config(4, 1, 0, 0, None, 0, 3), spk.spk_config(4, 1, 0, 0, None, 65, 3),
-                spk.spk_config(5, 1, 0, 0, None, 32, 2), spk.spk_config(5, 1, 0, 0, None, 32, 6)):
+                spk.spk_config(5, 1, 0, 0, None, 32, 2), spk.spk_config(5, 1, 0, 0, None, 32, 6),
+                spk.spk_config(2, 1, 3, 0, None, 32, 3), spk.spk_config(2, 1, 0, 0, None, 32, 3, 4),
+                spk.spk_config(2, 1, 2, 0, None, 32, 3, -1)):
         assert lib.spk_create(ctypes.byref(out), ctypes.byref(cfg)) == spk.SPK_ERR_ARG
         assert out.value is None
         assert spk.spk_last_error(None)
@@ -101,6 +103,12 @@ def test_noalloc_rejects_oversize_before_device_work(lib):
     rc = lib.spk_reconstruct_host_noalloc(ctypes.byref(cfg), st.ctypes.data, 1, 8, 4, float("nan"),
                                           out.ctypes.data)
     assert rc == spk.SPK_ERR_ARG
+    for theta in (1.5, 0.0, 65536.0):  # 8-bit frames need an integral threshold, 1 .. 65535
+        cfg8 = spk.spk_config(spk.SPK_SSR, 1, spk.SPK_U8, 0, None, 32, 3)
+        rc = lib.spk_reconstruct_host_noalloc(ctypes.byref(cfg8), st.ctypes.data, 1, 8, 4, theta,
+                                              out.ctypes.data)
+        assert rc == spk.SPK_ERR_ARG
+    assert "integral" in spk.spk_last_error(None)
     assert out[0] == -3.0
     with pytest.raises(ValueError):
         spk.spk_reconstruct_host_noalloc(st, 1000, 1000, 4000, 1.0, out)
