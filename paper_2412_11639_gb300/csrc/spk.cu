@@ -495,8 +495,17 @@ __device__ __forceinline__ void carry_store(int *c, int64_t P, int64_t p, const 
     c[19 * P] = npend > 1 ? fs.ri[fs.slot(pj + 1)] : 0;
 }
 
+// ORDER: 1 FSR, 2 SSR, 3 TFI, TREE_ORDER0 + n the n-order tree (n = 3..5 levels)
+constexpr int TREE_ORDER0 = 10;
+// The tree's first levels keep their node state in registers (7 nodes), deeper ones in local
+// memory.  n = 3 fits two blocks per SM in 96 registers (bench stream 12.8 ms; one block:
+// 14.7 ms); n = 4 and 5 take one (146 and 162 registers: 23.1 and 35.5 ms; two blocks with
+// spills: 33.4 and 56.8 ms).
+constexpr int TREE_REG_LEVELS = 3;
+constexpr int tree_min_blocks(int order) { return order == TREE_ORDER0 + 3 ? 2 : 1; }
+
 template <int ORDER, typename OutT, bool SEGMENTS, int MAXJ, int TT>
-__global__ void __launch_bounds__(NTHREADS, 3)
+__global__ void __launch_bounds__(NTHREADS, ORDER > TREE_ORDER0 ? tree_min_blocks(ORDER) : 3)
     spk_scan_kernel(const __grid_constant__ Batch<MAXJ> prm) {
     constexpr int WPT = TT / 32;  // 32-step words per tile
     extern __shared__ uint8_t smem_raw[];
@@ -542,12 +551,15 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     // ------------------------------------------------------------- compute warps ----
     const int64_t p = static_cast<int64_t>(blk) * BLOCK_PIX + warp * 32 + lane;
     const bool valid = p < job.P;
-    // ORDER 5 is the general n-order tree (job.order_n levels); 1 FSR, 2 SSR, 3 TFI
-    using Scan = std::conditional_t<ORDER == 5, spk::TreeScan, spk::PixelScan<ORDER == 5 ? 1 : ORDER>>;
+    constexpr bool TREE = ORDER > TREE_ORDER0;
+    constexpr int TN = TREE ? ORDER - TREE_ORDER0 : spk::TREE_MIN;
+    using Tree = spk::TreeScan<TN, TN < TREE_REG_LEVELS ? TN : TREE_REG_LEVELS>;
+    using Scan = std::conditional_t<TREE, Tree, spk::PixelScan<TREE ? 1 : ORDER>>;
     Scan sc;
-    if constexpr (ORDER == 5) {  // the pixel's ring: pend_cap (t, i) pairs, contiguous
+    int tree_deep[TREE ? Tree::NF * Tree::DEEPN : 1];  // the tree's deep levels (local memory)
+    if constexpr (TREE) {  // the pixel's ring: pend_cap (t, i) pairs, contiguous
         int *ring = prm.pend + static_cast<int64_t>(valid ? p : 0) * 2 * prm.pend_cap;
-        sc.init(job.order_n, ring, ring + 1, 2, prm.pend_cap);
+        sc.init(tree_deep, ring, ring + 1, 2, prm.pend_cap);
     } else {
         sc.init();
     }
@@ -572,7 +584,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         fs.cvb = 0;
         fs.zero_tail = (job.edges & EDGE_ZERO_TAIL) != 0;
         fs.cur_o = from_bits<OutT>(0);
-        if constexpr (ORDER != 5)
+        if constexpr (!TREE)
             if (!(job.flags & JOB_FIRST) && valid) carry_load(job.carry, job.P, p, sc, fs);
     }
 
@@ -620,7 +632,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
                     sc.spike(base + b, fs);
                 }
             }
-            if constexpr (ORDER == 5) {  // the tree's final cuts go to the sink in order
+            if constexpr (TREE) {  // the tree's final cuts go to the sink in order
                 if constexpr (SEGMENTS) sc.release(ss);
                 else sc.release(fs);
             }
@@ -640,13 +652,13 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         if (valid) prm.counts[p] = ss.cnt;
         // K, the number of spikes (S_1 has K - 1 elements, Def. 2): the scan's own count
         if (valid && prm.spikes) prm.spikes[p] = sc.last_t >= 0 ? sc.nint + 1 : 0;
-        if constexpr (ORDER == 5)
+        if constexpr (TREE)
             if (valid && sc.bad)
                 atomicOr(prm.status, (sc.bad & spk::TREE_BAD_ORDER ? DEV_INTERNAL : 0) |
                                          (sc.bad & spk::TREE_BAD_FULL ? DEV_PEND_FULL : 0));
     } else if (job.flags & JOB_LAST) {
         sc.finish(fs);
-        if constexpr (ORDER == 5)
+        if constexpr (TREE)
             if (valid && sc.bad)
                 atomicOr(prm.status, (sc.bad & spk::TREE_BAD_ORDER ? DEV_INTERNAL : 0) |
                                          (sc.bad & spk::TREE_BAD_FULL ? DEV_PEND_FULL : 0));
@@ -657,7 +669,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         // piece end: convert the final cuts and write every resolved frame; the last
         // converted cut starts the open span, the rest are pending candidates
         flush_rows(fs, sc.frontier(), valid, true);
-        if constexpr (ORDER != 5) {
+        if constexpr (!TREE) {
             if (valid) {
                 const int npend = fs.tail - fs.conv;
                 if (npend > 2 || fs.bad) atomicOr(prm.status, DEV_INTERNAL);
@@ -1068,20 +1080,18 @@ int launch_tfp(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
     return SPK_OK;
 }
 
-// the n-order tree runs single whole streams only (one job per launch).  Its node arrays are
-// dynamically indexed and live in local memory; for n = 3 a warp touches 56 words of them (7
-// KB), which fit in L1 if the kernel asks for the smallest shared-memory carveout that holds
-// one block: then one block runs per SM and its local memory stays in L1 (bench stream 76 ->
-// 50 ms).  Deeper trees touch too much for that to pay (n = 5: 165 -> 187 ms) and keep the
-// default carveout.  (The n-order calls are synchronous and never captured in a graph.)
+// the n-order tree runs single whole streams only (one job per launch), one kernel per
+// order, so that the tree's node state is indexed by constants and stays in registers.
+// (The n-order calls are synchronous and never captured in a graph.)
 template <typename OutT, bool SEG, int MAXJ>
 int launch_norder(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
     if constexpr (MAXJ == 1) {
-        auto kern = spk_scan_kernel<5, OutT, SEG, 1, TT_DEFAULT>;
-        const int carve = prm.jobs[0].order_n == 3 ? 45 : static_cast<int>(cudaSharedmemCarveoutDefault);
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve) != cudaSuccess)
-            return fail(ctx, SPK_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(cudaGetLastError()));
-        return launch<5, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
+        switch (prm.jobs[0].order_n) {
+            case 3: return launch<TREE_ORDER0 + 3, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
+            case 4: return launch<TREE_ORDER0 + 4, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
+            case 5: return launch<TREE_ORDER0 + 5, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
+            default: return fail(ctx, SPK_ERR_ARG, "stability_order must be 3..5");
+        }
     } else {
         return fail(ctx, SPK_ERR_ARG, "the n-order tree runs whole streams only");
     }
@@ -1143,7 +1153,7 @@ int tile_of(const spk_ctx *ctx, bool segments) {
 
 bool valid_method(const spk_config *cfg) {
     if (cfg->method < SPK_FSR || cfg->method > SPK_NORDER) return false;
-    if (cfg->method == SPK_NORDER) return cfg->stability_order >= 3 && cfg->stability_order <= spk::TREE_MAX;
+    if (cfg->method == SPK_NORDER) return cfg->stability_order >= spk::TREE_MIN && cfg->stability_order <= spk::TREE_MAX;
     return cfg->method != SPK_TFP || (cfg->tfp_window >= 1 && cfg->tfp_window <= 64);
 }
 

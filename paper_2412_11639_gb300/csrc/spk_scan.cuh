@@ -194,39 +194,94 @@ struct PixelScan {
 // ring of pcap entries (a power of two) in storage the caller provides, entry j of slot s
 // at pt[s * ps], pi[s * ps]; a push that finds it full sets bad bit 2 (the caller runs the
 // pixel again with a larger ring), an ordering fault bad bit 1.
-constexpr int TREE_MAX = 5;                       // deepest order
-constexpr int TREE_NODES = (1 << TREE_MAX) - 1;
+// The walk down the tree runs one block of code per LEVEL, not per node: a lane's node on
+// level L is r (0 .. 2^(L-1) - 1, heap index 2^(L-1) - 1 + r) and its state is gathered
+// from and scattered back to the level's nodes, so the lanes of a warp stay converged
+// whichever branches their elements take, and the code stays small.  The first RL levels
+// are indexed by constants only (select chains), so their state lives in registers; deeper
+// levels are indexed by r (per-thread local memory), for trees too large for registers.
+constexpr int TREE_MIN = 3, TREE_MAX = 5;  // orders of the tree (1 and 2 are PixelScan)
 constexpr int TREE_BAD_ORDER = 1;
 constexpr int TREE_BAD_FULL = 2;
 
+template <int N, int RL>
 struct TreeScan {
-    int n;                      // order (number of levels)
+    static_assert(N >= TREE_MIN && N <= TREE_MAX && RL >= 1 && RL <= N, "tree order");
+    static constexpr int NODES = (1 << N) - 1;
+    static constexpr int TOPN = (1 << RL) - 1;                          // nodes in registers
+    static constexpr int DEEPN = NODES > TOPN ? NODES - TOPN : 1;        // nodes in local memory
+    // per-node fields
+    enum { CNT,   // elements in the node's open sequence (0: none)
+           V0,    // its first value
+           V1,    // the other value (0: none yet)
+           Q0,    // last occurrence (node element index) of V0, -1: none
+           Q1,    // last occurrence of V1, -1: none
+           JN,    // next element index of the node's stream
+           PCT,   // cut after the node's latest element: spike time ...
+           PCI,   // ... and S_1 index
+           NF };
+    int top[NF][TOPN];          // levels 1 .. RL, heap order
+    int *deep;                  // levels RL+1 .. N: [NF][DEEPN] in the caller's per-thread
+                                // storage (kept out of this object, so that the object's
+                                // constant-indexed state is promoted to registers)
     int last_t, nint;           // S_1 bookkeeping, as in PixelScan
-    int cnt[TREE_NODES];        // elements in the node's open sequence (0: none)
-    int v0[TREE_NODES], v1[TREE_NODES];  // its first value and the other value (0: none yet)
-    int q0[TREE_NODES], q1[TREE_NODES];  // last occurrence (node element index) of v0 / v1, -1: none
-    int jn[TREE_NODES];         // next element index of the node's stream
-    int pct[TREE_NODES], pci[TREE_NODES];  // cut after the node's latest element
     int *pt, *pi;               // pending cuts, increasing t: a ring in the caller's storage
     int ps, pcap;               // its slot stride and capacity (a power of two)
     int ph, np;                 // first slot and number of pending cuts
+    int thead, tlast;           // times of the first and the last pending cut (np > 0)
     int rel_t;                  // last cut handed to the sink
     int bad;                    // TREE_BAD_FULL: the ring was too small; TREE_BAD_ORDER: a cut arrived behind the frontier
 
-    SPK_DEV void init(int order, int *pend_t, int *pend_i, int stride, int cap) {
-        n = order;
+    // field F of node r on level L
+    template <int L, int F>
+    SPK_DEV int get(int r) const {
+        constexpr int B = (1 << (L - 1)) - 1, M = 1 << (L - 1);
+        if constexpr (L > RL) {
+            return deep[F * DEEPN + B - TOPN + r];
+        } else if constexpr (M == 1) {
+            return top[F][B];
+        } else {
+            int v = top[F][B];
+#pragma unroll
+            for (int i = 1; i < M; ++i) v = r == i ? top[F][B + i] : v;
+            return v;
+        }
+    }
+    template <int L, int F>
+    SPK_DEV void put(int r, int v) {
+        constexpr int B = (1 << (L - 1)) - 1, M = 1 << (L - 1);
+        if constexpr (L > RL) {
+            deep[F * DEEPN + B - TOPN + r] = v;
+        } else if constexpr (M == 1) {
+            top[F][B] = v;
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+                if (r == i) top[F][B + i] = v;
+        }
+    }
+
+    SPK_DEV void init(int *deep_store, int *pend_t, int *pend_i, int stride, int cap) {
         last_t = -1;
         nint = 0;
-        for (int k = 0; k < TREE_NODES; ++k) {
-            cnt[k] = 0;
-            q0[k] = q1[k] = -1;
-            jn[k] = 0;
+#pragma unroll
+        for (int k = 0; k < TOPN; ++k) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) top[f][k] = 0;
+            top[Q0][k] = top[Q1][k] = -1;
         }
+        deep = deep_store;
+        if constexpr (NODES > TOPN)
+            for (int k = 0; k < DEEPN; ++k) {
+                for (int f = 0; f < NF; ++f) deep[f * DEEPN + k] = 0;
+                deep[Q0 * DEEPN + k] = deep[Q1 * DEEPN + k] = -1;
+            }
         pt = pend_t;
         pi = pend_i;
         ps = stride;
         pcap = cap;
         ph = np = 0;
+        thead = tlast = 0;
         rel_t = -1;
         bad = 0;
     }
@@ -240,29 +295,35 @@ struct TreeScan {
     // and (above the last level) its previous element was a 1 as well, so that each of the
     // 32 elements sends a distance of 1 one level down -- no node can break, and the word
     // is absorbed in O(levels).  Otherwise nothing changes and false is returned.
+    template <int L>
+    SPK_DEV bool ones_steady(int r) const {
+        const int a0 = get<L, V0>(r);
+        if (get<L, CNT>(r) == 0 || (a0 != 1 && get<L, V1>(r) != 1)) return false;
+        if constexpr (L < N) {
+            const int b = a0 == 1 ? 0 : 1;
+            if ((b ? get<L, Q1>(r) : get<L, Q0>(r)) != get<L, JN>(r) - 1) return false;
+            return ones_steady<L + 1>(2 * r + b);
+        } else {
+            return true;
+        }
+    }
+    template <int L>
+    SPK_DEV void ones_take(int r, int base) {
+        put<L, CNT>(r, get<L, CNT>(r) + 32);
+        put<L, PCT>(r, base + 31);
+        put<L, PCI>(r, nint + 31);
+        if constexpr (L < N) {
+            const int j = get<L, JN>(r) + 32;
+            put<L, JN>(r, j);
+            const int b = get<L, V0>(r) == 1 ? 0 : 1;
+            if (b) put<L, Q1>(r, j - 1);
+            else put<L, Q0>(r, j - 1);
+            ones_take<L + 1>(2 * r + b, base);
+        }
+    }
     SPK_DEV bool absorb_ones(int base) {
-        if (last_t != base - 1) return false;
-        int path[TREE_MAX];
-        int k = 0, levels = 0;
-        for (int level = 1;; ++level) {
-            if (cnt[k] == 0 || (v0[k] != 1 && v1[k] != 1)) return false;
-            path[levels++] = k;
-            if (level >= n) break;
-            const int b = v0[k] == 1 ? 0 : 1;
-            if ((b ? q1[k] : q0[k]) != jn[k] - 1) return false;
-            k = 2 * k + 1 + b;
-        }
-        for (int m = 0; m < levels; ++m) {
-            const int kk = path[m];
-            jn[kk] += 32;
-            cnt[kk] += 32;
-            pct[kk] = base + 31;
-            pci[kk] = nint + 31;
-            if (m + 1 < levels) {
-                if (v0[kk] == 1) q0[kk] = jn[kk] - 1;
-                else q1[kk] = jn[kk] - 1;
-            }
-        }
+        if (last_t != base - 1 || !ones_steady<1>(0)) return false;
+        ones_take<1>(0, base);
         nint += 32;
         last_t = base + 31;
         return true;
@@ -270,18 +331,29 @@ struct TreeScan {
 
     SPK_DEV int frontier() const {
         int S = last_t;
-        for (int k = 0; k < (1 << n) - 1; ++k)
-            if (cnt[k] && pct[k] < S) S = pct[k];
+#pragma unroll
+        for (int k = 0; k < TOPN; ++k)
+            if (top[CNT][k] && top[PCT][k] < S) S = top[PCT][k];
+        if constexpr (NODES > TOPN)
+            for (int k = 0; k < DEEPN; ++k)
+                if (deep[CNT * DEEPN + k] && deep[PCT * DEEPN + k] < S) S = deep[PCT * DEEPN + k];
         return S;
     }
+    // Most cuts come after every pending one (a level-1 break, or the first pending cut):
+    // they are appended without reading the ring, whose first and last times are kept in
+    // registers; only a cut that lands inside the list walks it.
     SPK_DEV void push(int t, int i) {
         if (t <= rel_t) {               // handed over already (equal) -- earlier would be a fault
             if (t < rel_t) bad |= TREE_BAD_ORDER;
             return;
         }
+        if (np > 0 && t == tlast) return;  // the same cut from two levels
         int j = np;
-        while (j > 0 && pt[slot(j - 1)] > t) --j;
-        if (j > 0 && pt[slot(j - 1)] == t) return;  // the same cut from two levels
+        if (np > 0 && t < tlast) {
+            --j;                         // the last entry is tlast > t
+            while (j > 0 && pt[slot(j - 1)] > t) --j;
+            if (j > 0 && pt[slot(j - 1)] == t) return;
+        }
         if (np == pcap) {
             bad |= TREE_BAD_FULL;
             return;
@@ -294,71 +366,88 @@ struct TreeScan {
         const int64_t s = slot(j);
         pt[s] = t;
         pi[s] = i;
+        if (j == 0) thead = t;
+        if (j == np) tlast = t;
         ++np;
     }
-    // the sequences of every descendant of node k (at `level`) end
-    SPK_DEV void reset_below(int k, int level) {
-        int lo = 2 * k + 1, hi = 2 * k + 2;  // nodes of the next level under k
-        for (int lev = level + 1; lev <= n; ++lev) {
-            for (int d = lo; d <= hi; ++d) {
-                cnt[d] = 0;
-                q0[d] = q1[d] = -1;
-            }
-            lo = 2 * lo + 1;
-            hi = 2 * hi + 2;
-        }
-    }
-    // element x, whose own cut is (ct, ci), arrives at node k of the given level; then the
-    // distance it closes travels down the branch of its value
-    SPK_DEV void element(int k, int level, int x, int ct, int ci) {
-        for (;;) {
-            const int j = jn[k]++;
-            if (cnt[k] == 0) {
-                v0[k] = x;
-                v1[k] = 0;
-            } else if (x != v0[k] && x != v1[k]) {
-                if (v1[k] == 0 && (x - v0[k] == 1 || v0[k] - x == 1)) {
-                    v1[k] = x;
-                } else {                     // zero-order rule broken: the sequence ends after
-                    push(pct[k], pci[k]);    // the previous element, x opens the next one
-                    v0[k] = x;
-                    v1[k] = 0;
-                    cnt[k] = 0;
-                    q0[k] = q1[k] = -1;
-                    reset_below(k, level);
+    // the sequences of every descendant of node r of level L end
+    template <int L>
+    SPK_DEV void reset_below(int r) {
+        if constexpr (L < N) {
+#pragma unroll
+            for (int M = L + 1; M <= N; ++M) {
+                const int B = (1 << (M - 1)) - 1;
+                if (M <= RL) {
+#pragma unroll
+                    for (int i = 0; i < (1 << (M - 1)); ++i)
+                        if ((i >> (M - L)) == r) {
+                            top[CNT][B + i] = 0;
+                            if (M < N) top[Q0][B + i] = top[Q1][B + i] = -1;
+                        }
+                } else {
+                    const int lo = B - TOPN + (r << (M - L));
+                    for (int i = 0; i < (1 << (M - L)); ++i) {
+                        deep[CNT * DEEPN + lo + i] = 0;
+                        if (M < N) deep[Q0 * DEEPN + lo + i] = deep[Q1 * DEEPN + lo + i] = -1;
+                    }
                 }
             }
-            ++cnt[k];
-            pct[k] = ct;
-            pci[k] = ci;
-            if (level >= n) return;
-            const int b = x == v0[k] ? 0 : 1;
-            const int prev = b ? q1[k] : q0[k];
-            if (b) q1[k] = j;
-            else q0[k] = j;
-            if (prev < 0) return;
-            x = j - prev;
-            k = 2 * k + 1 + b;
-            ++level;
+        }
+    }
+    // element x, whose own cut is (ct, ci), arrives at node r of level L; then the distance
+    // it closes travels down the branch of its value
+    template <int L>
+    SPK_DEV void element(int x, int r, int ct, int ci) {
+        int c = get<L, CNT>(r), a0 = get<L, V0>(r), a1 = get<L, V1>(r);
+        int b0 = -1, b1 = -1;
+        if constexpr (L < N) {
+            b0 = get<L, Q0>(r);
+            b1 = get<L, Q1>(r);
+        }
+        if (c == 0) {
+            a0 = x;
+            a1 = 0;
+        } else if (x != a0 && x != a1) {
+            if (a1 == 0 && (x - a0 == 1 || a0 - x == 1)) {
+                a1 = x;
+            } else {                     // zero-order rule broken: the sequence ends after
+                push(get<L, PCT>(r), get<L, PCI>(r));  // the previous element, x opens the next
+                a0 = x;
+                a1 = 0;
+                c = 0;
+                b0 = b1 = -1;
+                reset_below<L>(r);
+            }
+        }
+        put<L, CNT>(r, c + 1);
+        put<L, V0>(r, a0);
+        put<L, V1>(r, a1);
+        put<L, PCT>(r, ct);
+        put<L, PCI>(r, ci);
+        if constexpr (L < N) {
+            const int j = get<L, JN>(r);
+            put<L, JN>(r, j + 1);
+            const int b = x == a0 ? 0 : 1;
+            const int prev = b ? b1 : b0;
+            put<L, Q0>(r, b ? b0 : j);
+            put<L, Q1>(r, b ? j : b1);
+            if (prev >= 0) element<L + 1>(j - prev, 2 * r + b, ct, ci);
         }
     }
     template <class Sink>
     SPK_DEV void spike(int t, Sink &) {
-        element(0, 1, t - last_t, t, nint);
+        element<1>(t - last_t, 0, t, nint);
         ++nint;
         last_t = t;
     }
     // hand every final pending cut to the sink, in time order
     template <class Sink>
     SPK_DEV void release(Sink &sink, int S) {
-        while (np > 0) {
-            const int64_t s = slot(0);
-            const int t = pt[s];
-            if (t > S) break;
-            sink.cand(t, pi[s]);
-            rel_t = t;
+        while (np > 0 && thead <= S) {
+            sink.cand(thead, pi[slot(0)]);
+            rel_t = thead;
             ph = (ph + 1) & (pcap - 1);
-            --np;
+            if (--np > 0) thead = pt[slot(0)];
         }
     }
     template <class Sink>

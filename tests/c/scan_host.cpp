@@ -8,13 +8,15 @@
 //   * no candidate arrives before a frontier() reported after an earlier word, and no two
 //     cuts share a time (so a record at or before the frontier is final).
 //
-// usage: scan_host <stream.bin> <P> <T> <pitch> <order 1..5> <out.bin>
-// (1 FSR, 2 SSR: PixelScan; 3..5: the general n-order tree TreeScan of the same header)
+// usage: scan_host <stream.bin> <P> <T> <pitch> <order 1..5>[l] <out.bin>
+// (1 FSR, 2 SSR: PixelScan; 3..5: the n-order tree TreeScan<n, 3> of the same header, its
+// first three levels' node state indexed by constants; with the suffix l, TreeScan<n, 1>)
 // stream.bin: uint8 [T][pitch], pixel p is bit p % 8 of byte p / 8 (the library's layout).
 // out.bin: int32 counts[P], then for every pixel in order its sequences as int32 triples
 // (t_start, t_end, n_intervals).  Exit status 0, or 3 if a property above failed.
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <cstdlib>
 #include <vector>
 
@@ -94,13 +96,15 @@ int run(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, FILE *ou
 // increasing and the tree's ordering flag must stay clear.  The pending-cut ring holds
 // `cap` cuts; a pixel that needs more sets the tree's full flag (exit status 4), and the
 // largest number of cuts pending at a word end over all pixels goes to stderr.
-int run_tree(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, int n, int cap, FILE *out) {
+template <int N, int RL>
+int run_tree(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, int cap, FILE *out) {
     std::vector<int32_t> counts(P, 0), spans;
     std::vector<int> pend_t(cap), pend_i(cap);
     int bad = 0, max_np = 0;
-    auto *sc = new spk::TreeScan;  // about 1 KB of node arrays
+    auto *sc = new spk::TreeScan<N, RL>;
+    std::vector<int> deep(spk::TreeScan<N, RL>::NF * spk::TreeScan<N, RL>::DEEPN);
     for (int64_t p = 0; p < P; ++p) {
-        sc->init(n, pend_t.data(), pend_i.data(), 1, cap);
+        sc->init(deep.data(), pend_t.data(), pend_i.data(), 1, cap);
         Cuts c;
         int t0 = -1;
         for (int base = 0; base < T; base += 32) {
@@ -147,7 +151,7 @@ int run_tree(const std::vector<uint8_t> &s, int64_t P, int T, int64_t pitch, int
 
 int main(int argc, char **argv) {
     if (argc != 7 && argc != 8) {
-        fprintf(stderr, "usage: scan_host stream.bin P T pitch order out.bin [ring capacity, orders 3..5]\n");
+        fprintf(stderr, "usage: scan_host stream.bin P T pitch order[l] out.bin [ring capacity, orders 3..5]\n");
         return 2;
     }
     const int cap = argc == 8 ? atoi(argv[7]) : 1 << 16;
@@ -157,6 +161,7 @@ int main(int argc, char **argv) {
     }
     const int64_t P = atoll(argv[2]), pitch = atoll(argv[4]);
     const int T = atoi(argv[3]), order = atoi(argv[5]);
+    const bool reg = strchr(argv[5], 'l') == nullptr;  // "3l": every level's node state indexed by node
     std::vector<uint8_t> s(static_cast<size_t>(pitch) * T);
     FILE *f = fopen(argv[1], "rb");
     if (!f || fread(s.data(), 1, s.size(), f) != s.size()) return 2;
@@ -166,7 +171,12 @@ int main(int argc, char **argv) {
     if (order < 1 || order > spk::TREE_MAX) return 2;
     const int bad = order == 1   ? run<1>(s, P, T, pitch, out)
                     : order == 2 ? run<2>(s, P, T, pitch, out)
-                                 : run_tree(s, P, T, pitch, order, cap, out);
+                    : order == 3 ? (reg ? run_tree<3, 3>(s, P, T, pitch, cap, out)
+                                        : run_tree<3, 1>(s, P, T, pitch, cap, out))
+                    : order == 4 ? (reg ? run_tree<4, 3>(s, P, T, pitch, cap, out)
+                                        : run_tree<4, 1>(s, P, T, pitch, cap, out))
+                                 : (reg ? run_tree<5, 3>(s, P, T, pitch, cap, out)
+                                        : run_tree<5, 1>(s, P, T, pitch, cap, out));
     fclose(out);
     if (bad)
         fprintf(stderr, "property failed: %s%s%s\n", bad & 1 ? "order " : "", bad & 2 ? "frontier " : "",

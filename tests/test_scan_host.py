@@ -29,11 +29,11 @@ def scan_host(tmp_path_factory):
     return exe
 
 
-def run_host(exe, tmp_path, st, P, T, order, ring=None):
+def run_host(exe, tmp_path, st, P, T, order, ring=None, layout=""):
     st = np.ascontiguousarray(st, dtype=np.uint8)
     src, dst = tmp_path / "stream.bin", tmp_path / "spans.bin"
     st.tofile(src)
-    r = subprocess.run([exe, str(src), str(P), str(T), str(st.shape[1]), str(order), str(dst)]
+    r = subprocess.run([exe, str(src), str(P), str(T), str(st.shape[1]), f"{order}{layout}", str(dst)]
                        + ([str(ring)] if ring else []), capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     raw = np.fromfile(dst, dtype=np.int32)
@@ -43,9 +43,9 @@ def run_host(exe, tmp_path, st, P, T, order, ring=None):
     return counts, spans
 
 
-def check_against_oracle(exe, tmp_path, st, H, W, T, order):
+def check_against_oracle(exe, tmp_path, st, H, W, T, order, layout=""):
     P = H * W
-    counts, spans = run_host(exe, tmp_path, st, P, T, order)
+    counts, spans = run_host(exe, tmp_path, st, P, T, order, layout=layout)
     ref = oracle.reconstruct(st, H, W, T, 1.0, order, 1, frames=False, segments=True)
     assert np.array_equal(counts, ref.nseg), "sequence counts differ"
     assert np.array_equal(spans[:, 0], ref.seg_ts), "sequence starts differ"
@@ -88,26 +88,29 @@ def test_scan_equals_oracle_on_every_16_step_pattern(scan_host, tmp_path, order)
     check_against_oracle(scan_host, tmp_path, st, 256, 256, T, order)
 
 
+@pytest.mark.parametrize("layout", ["", "l"])
 @pytest.mark.parametrize("order", [3, 4, 5])
 @pytest.mark.parametrize("recipe,H,W,T", [
     ("dynamic_250x400x20000", 12, 40, 2500),
     ("large_1000x1000x20000", 10, 40, 2000),
 ])
-def test_tree_equals_oracle_on_scenes(scan_host, tmp_path, recipe, H, W, T, order):
-    """The n-order tree (Fig. 1 caption, Sec. III-B) of the same header, orders 3..5."""
+def test_tree_equals_oracle_on_scenes(scan_host, tmp_path, recipe, H, W, T, order, layout):
+    """The n-order tree (Fig. 1 caption, Sec. III-B) of the same header, orders 3..5, with
+    its node state in constant-indexed registers and indexed by node (local memory)."""
     w = spkgen.WORKLOADS[recipe].resized(H=H, W=W, T=T)
     st, _ = spkgen.make_stream(w)
-    counts = check_against_oracle(scan_host, tmp_path, st, H, W, T, order)
+    counts = check_against_oracle(scan_host, tmp_path, st, H, W, T, order, layout)
     assert counts.sum() > 10 * H * W
 
 
+@pytest.mark.parametrize("layout", ["", "l"])
 @pytest.mark.parametrize("order", [3, 5])
 @pytest.mark.parametrize("density", [0.3, 0.7, 0.95])
-def test_tree_equals_oracle_on_random_bits(scan_host, tmp_path, density, order):
+def test_tree_equals_oracle_on_random_bits(scan_host, tmp_path, density, order, layout):
     H, W, T = 8, 40, 1200
     bits = spkgen.random_bits(T, H * W, density, seed=int(density * 1000) + 10 * order)
     st = spkgen.pack(bits, H, W)
-    check_against_oracle(scan_host, tmp_path, st, H, W, T, order)
+    check_against_oracle(scan_host, tmp_path, st, H, W, T, order, layout)
 
 
 @pytest.mark.parametrize("order", [3, 5])
