@@ -74,12 +74,13 @@ enum spk_edges { SPK_ZERO_HEAD = 1, SPK_ZERO_TAIL = 2 };
  *           stable sequence of a level-k stream the '-' and '+' streams of its two values
  *           (index distances between their occurrences) are segmented by the same rule,
  *           and each of their breaks cuts the level above after the element where the
- *           breaking distance ends.  Whole streams only (no spk_stream / spk_run).  Cuts
- *           of deep levels wait in a per-pixel ring (64 cuts at first, owned by the
- *           context) until no earlier cut can appear; if a pixel needs more, the call runs
- *           again with rings twice as large, so every valid stream is reconstructed.  For
- *           this method spk_reconstruct and spk_segments therefore wait for the device
- *           (synchronous) and can also return SPK_ERR_OOM. */
+ *           breaking distance ends.  Whole streams only (no spk_stream; spk_run takes
+ *           batches of whole streams).  Cuts of deep levels wait in a per-pixel ring (64
+ *           cuts, 512 bytes, per pixel at first, owned by the context) until no earlier
+ *           cut can appear; if a pixel needs more, the call runs again with rings twice as
+ *           large, so every valid stream is reconstructed.  For this method
+ *           spk_reconstruct, spk_segments and spk_run therefore wait for the device
+ *           (synchronous; not for stream capture) and can also return SPK_ERR_OOM. */
 enum spk_method { SPK_FSR = 1, SPK_SSR = 2, SPK_TFI = 3, SPK_TFP = 4, SPK_NORDER = 5 };
 
 typedef struct spk_config {
@@ -190,8 +191,10 @@ typedef struct spk_job {
  * uneven size and length -- and the next pieces of many live streams -- are processed
  * together.  Each job gives the frames of Sec. III-B exactly as spk_reconstruct would.
  * A stream may appear at most once per call; outputs of different jobs must not overlap.
- * Asynchronous on ctx's stream.  Errors: SPK_ERR_ARG (bad job, piece past the stream's T,
- * repeated stream), SPK_ERR_CUDA. */
+ * Asynchronous on ctx's stream (synchronous for SPK_NORDER, whose jobs must be whole
+ * streams; see spk_method).  Errors: SPK_ERR_ARG (bad job, piece past the stream's T,
+ * repeated stream, a live stream with TFP or SPK_NORDER), SPK_ERR_CUDA, and for SPK_NORDER
+ * SPK_ERR_OOM. */
 int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs);
 
 /* Time tile of the frames kernels: the steps one TMA box stages per block (32, 64 or 128;

@@ -94,6 +94,7 @@ struct Job {
     int edges;      // frame edge policy (EDGE_ZERO_HEAD | EDGE_ZERO_TAIL)
     int flags;      // JOB_FIRST | JOB_LAST
     int block0;     // first block of this job in the flat grid
+    int64_t pend_px;  // n-order tree: the job's first pixel in the batch's pending-cut rings
 };
 
 template <int MAXJ>
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(NTHREADS, ORDER > TREE_ORDER0 ? tree_min_block
     Scan sc;
     int tree_deep[TREE ? Tree::NF * Tree::DEEPN : 1];  // the tree's deep levels (local memory)
     if constexpr (TREE) {  // the pixel's ring: pend_cap (t, i) pairs, contiguous
-        int *ring = prm.pend + static_cast<int64_t>(valid ? p : 0) * 2 * prm.pend_cap;
+        int *ring = prm.pend + (job.pend_px + (valid ? p : 0)) * 2 * prm.pend_cap;
         sc.init(tree_deep, ring, ring + 1, 2, prm.pend_cap);
     } else {
         sc.init();
@@ -1085,15 +1086,15 @@ int launch_tfp(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
 // (The n-order calls are synchronous and never captured in a graph.)
 template <typename OutT, bool SEG, int MAXJ>
 int launch_norder(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
-    if constexpr (MAXJ == 1) {
+    if constexpr (SEG && MAXJ > 1) {
+        return fail(ctx, SPK_ERR_ARG, "segments are exported for one stream at a time");
+    } else {
         switch (prm.jobs[0].order_n) {
-            case 3: return launch<TREE_ORDER0 + 3, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
-            case 4: return launch<TREE_ORDER0 + 4, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
-            case 5: return launch<TREE_ORDER0 + 5, OutT, SEG, 1, TT_DEFAULT>(ctx, prm, nblocks);
+            case 3: return launch<TREE_ORDER0 + 3, OutT, SEG, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+            case 4: return launch<TREE_ORDER0 + 4, OutT, SEG, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+            case 5: return launch<TREE_ORDER0 + 5, OutT, SEG, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
             default: return fail(ctx, SPK_ERR_ARG, "stability_order must be 3..5");
         }
-    } else {
-        return fail(ctx, SPK_ERR_ARG, "the n-order tree runs whole streams only");
     }
 }
 
@@ -1190,6 +1191,46 @@ int fill_job(spk_ctx *ctx, CUtensorMap *map, Job *job, const uint8_t *stream, in
     return static_cast<int>((P + BLOCK_PIX - 1) / BLOCK_PIX);
 }
 
+// The n-order tree holds cuts that are not final yet in a per-pixel ring (npix pixels over
+// the launch's jobs, each job's from its pend_px on).  A pixel whose ring runs full reports
+// it; the launch then runs again with rings twice as large, so every valid stream is
+// reconstructed (at most T_max + 1 cuts can be pending; the jobs are whole streams, so a
+// rerun rewrites every output).  Synchronous.
+template <int MAXJ>
+int run_norder(spk_ctx *ctx, Batch<MAXJ> &prm, int nblocks, bool segments, int64_t npix, int T_max) {
+    int pcap = g_norder_cap0.load();
+    for (;;) {
+        const size_t need = static_cast<size_t>(2) * static_cast<size_t>(pcap) * static_cast<size_t>(npix) * sizeof(int);
+        if (need > ctx->pend_bytes) {
+            if (ctx->pend_fixed)
+                return fail(ctx, SPK_ERR_INTERNAL, "n-order pending cuts need %zu bytes of rings, %zu available", need,
+                            ctx->pend_bytes);
+            if (ctx->d_pend) cudaFree(ctx->d_pend);
+            ctx->d_pend = nullptr;
+            ctx->pend_bytes = 0;
+            if (dev_malloc(&ctx->d_pend, need) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) of the n-order pending-cut rings failed", need);
+            }
+            ctx->pend_bytes = need;
+        }
+        prm.pend = ctx->d_pend;
+        prm.pend_cap = pcap;
+        int rc = dispatch(ctx, prm, nblocks, segments, TT_DEFAULT);
+        if (rc) return rc;
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+        int st = 0;
+        if (cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(ctx, SPK_ERR_CUDA, "status read failed");
+        if (st != DEV_PEND_FULL) return SPK_OK;  // done, or another failure for spk_synchronize to report
+        if (static_cast<int64_t>(pcap) > T_max) return fail(ctx, SPK_ERR_INTERNAL, "n-order pending cuts exceed T");
+        if (cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess)
+            return fail(ctx, SPK_ERR_CUDA, "status reset failed");
+        pcap *= 2;
+    }
+}
+
 int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float threshold, void *out,
              int32_t *spikes, int32_t *counts, int32_t *ts, int32_t *te, int32_t *n, float *v, int cap,
              bool segments) {
@@ -1209,42 +1250,7 @@ int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float thr
     prm.seg_v = v;
     prm.cap = cap;
     if (ctx->cfg.method != SPK_NORDER) return dispatch(ctx, prm, nb, segments, tile);
-
-    // The n-order tree holds cuts that are not final yet in a per-pixel ring.  A pixel whose
-    // ring runs full reports it; the call then runs again with rings twice as large, so every
-    // valid stream is reconstructed (at most T + 1 cuts can be pending).  Synchronous.
-    const int64_t P = static_cast<int64_t>(H) * W;
-    int pcap = g_norder_cap0.load();
-    for (;;) {
-        const size_t need = static_cast<size_t>(2) * static_cast<size_t>(pcap) * static_cast<size_t>(P) * sizeof(int);
-        if (need > ctx->pend_bytes) {
-            if (ctx->pend_fixed)
-                return fail(ctx, SPK_ERR_INTERNAL, "n-order pending cuts need %zu bytes of rings, %zu available", need,
-                            ctx->pend_bytes);
-            if (ctx->d_pend) cudaFree(ctx->d_pend);
-            ctx->d_pend = nullptr;
-            ctx->pend_bytes = 0;
-            if (dev_malloc(&ctx->d_pend, need) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) of the n-order pending-cut rings failed", need);
-            }
-            ctx->pend_bytes = need;
-        }
-        prm.pend = ctx->d_pend;
-        prm.pend_cap = pcap;
-        int rc = dispatch(ctx, prm, nb, segments, tile);
-        if (rc) return rc;
-        cudaError_t e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
-        int st = 0;
-        if (cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-            return fail(ctx, SPK_ERR_CUDA, "status read failed");
-        if (st != DEV_PEND_FULL) return SPK_OK;  // done, or another failure for spk_synchronize to report
-        if (static_cast<int64_t>(pcap) > T) return fail(ctx, SPK_ERR_INTERNAL, "n-order pending cuts exceed T");
-        if (cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess)
-            return fail(ctx, SPK_ERR_CUDA, "status reset failed");
-        pcap *= 2;
-    }
+    return run_norder(ctx, prm, nb, segments, static_cast<int64_t>(H) * W, T);
 }
 
 bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
@@ -1452,7 +1458,7 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
             return fail(ctx, SPK_ERR_ARG, "job %d: stream and out_frames must be device memory", k);
         if (jb.state) {
             if (ctx->cfg.method == SPK_TFP || ctx->cfg.method == SPK_NORDER)
-        return fail(ctx, SPK_ERR_ARG, "TFP and the n-order tree run whole streams only");
+                return fail(ctx, SPK_ERR_ARG, "TFP and the n-order tree run whole streams only");
             if (jb.state->H != jb.H || jb.state->W != jb.W) return fail(ctx, SPK_ERR_ARG, "job %d: H, W differ from its stream", k);
             if (jb.state->pushed + jb.n > jb.state->T) return fail(ctx, SPK_ERR_ARG, "job %d: piece runs past the stream's T", k);
             if (jb.state->device != ctx->cfg.device) return fail(ctx, SPK_ERR_ARG, "job %d: stream on another device", k);
@@ -1482,7 +1488,8 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
     int rc = SPK_OK;
     for (int k0 = 0; k0 < njobs && rc == SPK_OK; k0 += MAXJ_BATCH) {
         const int nj = njobs - k0 < MAXJ_BATCH ? njobs - k0 : MAXJ_BATCH;
-        int blocks = 0;
+        int blocks = 0, T_max = 0;
+        int64_t npix = 0;
         for (int k = 0; k < nj && rc == SPK_OK; ++k) {
             const spk_job &jb = jobs[order[k0 + k]];
             spk_stream *st = jb.state;
@@ -1497,13 +1504,20 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
             const int nb = fill_job(ctx, &prm->maps[k], &prm->jobs[k], jb.stream, jb.H, jb.W, jb.n, t_base, T,
                                     jb.threshold, jb.out_frames, st ? st->d_carry : nullptr,
                                     st ? st->d_ready : nullptr, flags, blocks, tile_of(ctx, false));
-            if (nb < 0) rc = nb;
-            else blocks += nb;
+            if (nb < 0) {
+                rc = nb;
+            } else {
+                blocks += nb;
+                prm->jobs[k].pend_px = npix;  // the n-order tree's rings, job after job
+                npix += static_cast<int64_t>(jb.H) * jb.W;
+                if (jb.n > T_max) T_max = jb.n;
+            }
         }
         if (rc) break;
         prm->njobs = nj;
         prm->status = ctx->d_status;
-        rc = dispatch(ctx, *prm, blocks, false, tile_of(ctx, false));
+        rc = ctx->cfg.method == SPK_NORDER ? run_norder(ctx, *prm, blocks, false, npix, T_max)
+                                           : dispatch(ctx, *prm, blocks, false, tile_of(ctx, false));
         if (rc == SPK_OK)
             for (int k = 0; k < nj; ++k)
                 if (jobs[order[k0 + k]].state) jobs[order[k0 + k]].state->pushed += jobs[order[k0 + k]].n;

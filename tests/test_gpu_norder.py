@@ -93,13 +93,53 @@ def test_norder_scene_workload(env, n):
 
 
 def test_norder_runs_whole_streams_only(env):
+    """Live streams are refused (the tree's state is not carried between pieces)."""
     from paper_2412_11639_gb300 import spk
     R = env.Reconstructor(order=5, stability_order=3)
-    dev = torch.zeros((100, spkgen.pitch(4, 8)), dtype=torch.uint8, device="cuda")
-    out = R.alloc_frames(4, 8, 100)
     with pytest.raises(spk.SpkError):
-        env.spk_run(R.ctx, [(dev, 4, 8, 100, 1.0, out, None)])
+        env.Stream(R, 4, 8, 100)
     R.close()
+
+
+@pytest.mark.parametrize("n,ring0", [(3, 0), (4, 0), (5, 0), (3, 2), (5, 2)])
+def test_norder_batch_of_uneven_streams(env, n, ring0):
+    """spk_run: whole streams of uneven size in one launch (each job's pending-cut rings
+    after the previous job's).  Every job equals its stream alone bit for bit and the
+    oracle within 1e-6; started with rings of 2 cuts, the whole batch runs again with
+    larger rings until every pixel fits."""
+    from paper_2412_11639_gb300 import spk
+    rng = np.random.default_rng(40 + n)
+    spk.spk_debug_norder_capacity(ring0)
+    try:
+        R = env.Reconstructor(order=5, stability_order=n, stride=3)
+        jobs, keep = [], []
+        for k in range(8):
+            H, W, T = int(rng.integers(1, 20)), int(rng.integers(1, 70)), int(rng.integers(1, 2500))
+            if k == 0:                   # a scene whose deep cuts need rings of more than 4
+                H, W, T = 12, 70, 3000
+            if k % 2 == 0:
+                w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=H, W=W, T=T)
+                st = spkgen.make_stream(w)[0]
+            else:
+                st = spkgen.pack(_deep_streams(H * W, T, seed=k), H, W)
+            d = torch.from_numpy(np.ascontiguousarray(st)).cuda()
+            o = R.alloc_frames(H, W, T)
+            jobs.append((d, H, W, T, 1.0, o, None))
+            keep.append((st, d, H, W, T, o))
+        n0 = spk.spk_launch_count(R.ctx)
+        env.spk_run(R.ctx, jobs)
+        R.synchronize()
+        launches = spk.spk_launch_count(R.ctx) - n0
+        assert launches == 1 if ring0 == 0 else launches >= 2
+        for st, d, H, W, T, o in keep:
+            got = o.cpu().numpy().reshape(-1, H * W)
+            alone = R(d, H, W, T).cpu().numpy().reshape(-1, H * W)
+            assert np.array_equal(got.view(np.uint32), alone.view(np.uint32)), (H, W, T)
+            r = oracle.reconstruct(st, H, W, T, 1.0, n, 3)
+            assert np.all(np.abs(got - r.frames) <= REL_TOL * np.abs(r.frames)), (H, W, T)
+        R.close()
+    finally:
+        spk.spk_debug_norder_capacity(0)
 
 
 @pytest.mark.parametrize("n", [3, 5])
