@@ -340,6 +340,40 @@ def large_sensor_record(local_rank: int, order: int, steps: int = 3, warmup: int
                          "kernel": KERNEL, "kernel_ms": ms, "algorithmic_bytes_per_launch": alg_bytes}}
 
 
+def methods_record(dev, w, local_rank: int, steps: int = 5, warmup: int = 3):
+    """The other reconstruction methods on the same resident stream and frame layout (FSR,
+    the TFI and TFP baselines, the n-order tree at n = 3, 4, 5), each timed with CUDA events
+    on its launching stream."""
+    import torch
+
+    import paper_2412_11639_gb300 as pkg
+    from paper_2412_11639_gb300 import spk
+    dtype = torch.float16 if w.out_dtype == "f16" else torch.float32
+    rec = {}
+    for name, order, n in (("FSR", 1, 3), ("TFI", 3, 3), ("TFP-32", 4, 3), ("n-order n=3", 5, 3),
+                           ("n-order n=4", 5, 4), ("n-order n=5", 5, 5)):
+        R = pkg.Reconstructor(order=order, stride=w.stride, dtype=dtype, device=local_rank,
+                              tfp_window=32, stability_order=n)
+        out = R.alloc_frames(w.H, w.W, w.T)
+        for _ in range(warmup):
+            R(dev, w.H, w.W, w.T, 1.0, out=out)
+        R.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        n0 = spk.spk_launch_count(R.ctx)
+        for a, b in ev:
+            a.record(R.stream)
+            R(dev, w.H, w.W, w.T, 1.0, out=out)
+            b.record(R.stream)
+        torch.cuda.synchronize()
+        R.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        rec[name] = {"ms_per_step": ms, "value": w.P * w.T_out / (ms / 1e3) / 1e9, "unit": UNIT,
+                     "gpu_launches": spk.spk_launch_count(R.ctx) - n0, "steps": steps}
+        R.close()
+        del out
+    return {"workload": w.name, "out_dtype": w.out_dtype, "frame_stride": w.stride, "methods": rec}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -431,9 +465,10 @@ def run_ours(args, rank, world, local_rank):
         else:
             refined = {"unavailable": "no trained checkpoint in the package"}
 
-    large = None
+    large = methods = None
     if (rank == 0 and not args.no_large and w.name == "dynamic_250x400x20000" and not args.T
             and not args.rows and args.order in (1, 2)):
+        methods = methods_record(dev, w, local_rank)
         large = large_sensor_record(local_rank, args.order)
 
     if rank != 0:
@@ -476,6 +511,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "refiner": refined,
         "large_sensor": large,
+        "other_methods": methods,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -284,6 +284,7 @@ struct FrameSink {
             int ke;
             if (t == TAIL) {
                 ke = T_out - 1;
+                if (zero_tail) cvb = 0;
             } else {
                 const int i = ri[s];
                 cvb = value_bits<OutT>(theta, i - ci, t - ct);
@@ -292,7 +293,7 @@ struct FrameSink {
                 ke = frame_of(t);
             }
             rt[s] = ke;
-            ri[s] = (t == TAIL && zero_tail) ? 0 : cvb;
+            ri[s] = cvb;
             kf = max(kf, ke + 1);
         }
     }
