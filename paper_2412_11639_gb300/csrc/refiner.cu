@@ -180,7 +180,7 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-constexpr int RING = 6;  // input-row slots
+constexpr int RING = 5;  // input-row slots
 constexpr int TMA_PX = 32;                  // pixels per main TMA box (256 bf16: the largest box edge)
 constexpr int TAIL_PX = 8;                  // pixels of the last box of a plane (pixels 128 .. 135)
 constexpr int HALO_PX = 4 * TMA_PX + TAIL_PX;  // pixels loaded per halo row (>= 130), 136 x 16 B = 17 x 128 B
@@ -204,7 +204,7 @@ struct ConvSmem {
 // and write the output rows; warp 4 (one thread) loads halo rows with TMA into the ring;
 // warp 5 (one thread) issues the MMAs, and allocates / frees the tensor memory.
 template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(192) conv3x3_kernel(const __grid_constant__ CUtensorMap xmap,
+__global__ void __launch_bounds__(192, 4) conv3x3_kernel(const __grid_constant__ CUtensorMap xmap,
                                                       const __grid_constant__ CUtensorMap xmap_tail,
                                                       const bf16 *__restrict__ Wt, const float *__restrict__ bias,
                                                       void *Y, const bf16 *__restrict__ mask,
