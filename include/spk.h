@@ -244,7 +244,7 @@ int64_t spk_launch_count(const spk_ctx *ctx);
  * that reads, per pixel and frame, the plain reconstruction and the rates theta / x of the
  * last four intervals, and returns plain + a learned correction.  Trained with the mean
  * squared error to a ground-truth intensity (Adam).  The plain frames remain the
- * fallback and the reference its error is judged against. */
+ * fallback and the reference its error is measured against. */
 
 /* Refiner input for every frame of a stream: device bf16, 16 channels per pixel stored as
  * two channel-chunk planes, [T_out][H][2][W][8] (channel c of pixel (y, x) of frame k at
