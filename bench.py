@@ -211,8 +211,9 @@ def kernel_source_sha() -> str:
 
 
 def recorded_profile(workload: str, order: int):
-    """(DRAM bytes per launch, ALU-pipe busy % of peak) from the committed ncu summary, if it
-    matches this source and workload; (None, None) otherwise."""
+    """Figures of the committed ncu capture, if it matches this source and workload (an empty
+    dict otherwise): DRAM bytes per launch, ALU-pipe busy % of peak, ALU-pipe warp
+    instructions per launch and the pipe's peak warp instructions per cycle (whole GPU)."""
     try:
         kv = {}
         for line in open(TRAFFIC_FILE):
@@ -221,11 +222,32 @@ def recorded_profile(workload: str, order: int):
                 kv[k.strip()] = v.strip()
         if (kv.get("workload") == workload and int(kv.get("order", -1)) == order
                 and kv.get("source_sha256") == kernel_source_sha()):
-            alu = kv.get("alu_pipe_active_pct")
-            return float(kv["dram_bytes_per_launch"]), (float(alu) if alu else None)
+            out = {"traffic": float(kv["dram_bytes_per_launch"])}
+            for key, name in (("alu_pipe_active_pct", "alu_pct"), ("alu_warp_inst_per_launch", "alu_inst"),
+                              ("alu_peak_warp_inst_per_cycle", "alu_peak_per_cycle")):
+                if kv.get(key):
+                    out[name] = float(kv[key])
+            return out
     except (OSError, ValueError, KeyError):
         pass
-    return None, None
+    return {}
+
+
+def alu_roofline(rec: dict, kern_ms: float, clk) -> dict | None:
+    """The scan's binding unit, the integer ALU pipe: ALU-pipe warp instructions per launch
+    (from the committed capture of this source) over the live kernel time, against the
+    pipe's peak (warp instructions per cycle for the whole GPU, from the same capture) at
+    the SM clock sampled during the timed region (2070 MHz, the maximum, if unsampled)."""
+    if "alu_inst" not in rec or "alu_peak_per_cycle" not in rec:
+        return None
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    achieved = rec["alu_inst"] / (kern_ms / 1e3) / 1e9
+    peak = rec["alu_peak_per_cycle"] * mhz * 1e6 / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s",
+            "frac": achieved / peak, "kernel": KERNEL, "kernel_ms": kern_ms,
+            "alu_warp_inst_per_launch": rec["alu_inst"], "sm_mhz": mhz,
+            "peak_source": "sm__inst_executed_pipe_alu.sum.peak_sustained x sampled SM clock",
+            "from_committed_capture": os.path.relpath(TRAFFIC_FILE, ROOT)}
 
 
 # ------------------------------------------------------------------ CPU oracle ----
@@ -487,7 +509,8 @@ def run_ours(args, rank, world, local_rank):
         oracle.set_threads(0)
         cpu["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
                               "sample": f"{n1} pixels x {w.T_out} frames, {dt1:.1f} s"}
-    traffic, alu_pct = recorded_profile(w.name, args.order)
+    rec = recorded_profile(w.name, args.order)
+    traffic, alu_pct = rec.get("traffic"), rec.get("alu_pct")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "input_Gpixel_steps_per_s": w.P * w.T * K * world / (total_ms / 1e3) / 1e9,
@@ -505,6 +528,7 @@ def run_ours(args, rank, world, local_rank):
                      "from_committed_capture": {
                          "file": os.path.relpath(TRAFFIC_FILE, ROOT), "fields": ["traffic"],
                          "alu_pipe_busy_pct_of_peak": alu_pct}},
+        "alu_roofline": alu_roofline(rec, kern_ms, clk),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
