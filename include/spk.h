@@ -74,13 +74,14 @@ enum spk_edges { SPK_ZERO_HEAD = 1, SPK_ZERO_TAIL = 2 };
  *           stable sequence of a level-k stream the '-' and '+' streams of its two values
  *           (index distances between their occurrences) are segmented by the same rule,
  *           and each of their breaks cuts the level above after the element where the
- *           breaking distance ends.  Whole streams only (no spk_stream; spk_run takes
- *           batches of whole streams).  Cuts of deep levels wait in a per-pixel ring (64
- *           cuts, 512 bytes, per pixel at first, owned by the context) until no earlier
- *           cut can appear; if a pixel needs more, the call runs again with rings twice as
- *           large, so every valid stream is reconstructed.  For this method
- *           spk_reconstruct, spk_segments and spk_run therefore wait for the device
- *           (synchronous; not for stream capture) and can also return SPK_ERR_OOM. */
+ *           breaking distance ends.  Cuts of deep levels wait in a per-pixel ring (64 cuts,
+ *           512 bytes, per pixel at first; owned by the context, or by a live stream, where
+ *           they stay pending from piece to piece) until no earlier cut can appear; if a
+ *           pixel needs more, the launch runs again with rings twice as large (a live
+ *           stream's piece from a copy of its state taken before the launch), so every
+ *           valid stream is reconstructed.  For this method spk_reconstruct, spk_segments
+ *           and spk_run therefore wait for the device (synchronous; not for stream capture)
+ *           and can also return SPK_ERR_OOM. */
 enum spk_method { SPK_FSR = 1, SPK_SSR = 2, SPK_TFI = 3, SPK_TFP = 4, SPK_NORDER = 5 };
 
 typedef struct spk_config {
@@ -155,11 +156,13 @@ int spk_reconstruct_host_async(spk_ctx *ctx, const uint8_t *host_stream, int H, 
  * same state across its 32-frame chunks. */
 typedef struct spk_stream spk_stream;
 
-/* Opens a stream of H x W pixels and T steps on ctx (its method -- FSR, SSR or TFI --,
- * frame stride and output type)
- * and allocates its device state: 20 int32 per pixel (the stability scan, the frames
- * already written, the cut that opens the current span, up to two pending cut
- * candidates) and one int32.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM. */
+/* Opens a stream of H x W pixels and T steps on ctx (its method -- FSR, SSR, TFI or the
+ * n-order tree --, frame stride and output type) and allocates its device state: 20 int32
+ * per pixel (the stability scan, the frames already written, the cut that opens the
+ * current span, up to two pending cut candidates) and one int32; for the n-order tree
+ * 11 + 8 x (7 + max(1, 2^n - 8)) int32 per pixel of scan and node state (75, 131, 259 for
+ * n = 3, 4, 5), its pending-cut rings (512 bytes per pixel at first), and a copy of both.
+ * TFP has no live streams.  Errors: SPK_ERR_ARG, SPK_ERR_CUDA, SPK_ERR_OOM. */
 int spk_stream_open(spk_ctx *ctx, int H, int W, int T, spk_stream **out);
 
 /* Waits for ctx's stream and frees the stream's device state.  NULL is a no-op. */
@@ -191,10 +194,9 @@ typedef struct spk_job {
  * uneven size and length -- and the next pieces of many live streams -- are processed
  * together.  Each job gives the frames of Sec. III-B exactly as spk_reconstruct would.
  * A stream may appear at most once per call; outputs of different jobs must not overlap.
- * Asynchronous on ctx's stream (synchronous for SPK_NORDER, whose jobs must be whole
- * streams; see spk_method).  Errors: SPK_ERR_ARG (bad job, piece past the stream's T,
- * repeated stream, a live stream with TFP or SPK_NORDER), SPK_ERR_CUDA, and for SPK_NORDER
- * SPK_ERR_OOM. */
+ * Asynchronous on ctx's stream (synchronous for SPK_NORDER; see spk_method).  Errors:
+ * SPK_ERR_ARG (bad job, piece past the stream's T, repeated stream, a live stream with TFP
+ * or opened for another method), SPK_ERR_CUDA, and for SPK_NORDER SPK_ERR_OOM. */
 int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs);
 
 /* Time tile of the frames kernels: the steps one TMA box stages per block (32, 64 or 128;

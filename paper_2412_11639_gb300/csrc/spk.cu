@@ -94,7 +94,9 @@ struct Job {
     int edges;      // frame edge policy (EDGE_ZERO_HEAD | EDGE_ZERO_TAIL)
     int flags;      // JOB_FIRST | JOB_LAST
     int block0;     // first block of this job in the flat grid
-    int64_t pend_px;  // n-order tree: the job's first pixel in the batch's pending-cut rings
+    int64_t pend_px;  // n-order tree, whole streams: the job's first pixel in the context's rings
+    int *pend;        // n-order tree: the job's pending-cut rings [P][pend_cap][2]
+    int pend_cap;
 };
 
 template <int MAXJ>
@@ -103,8 +105,6 @@ struct Batch {
     Job jobs[MAXJ];
     int njobs;
     int *status;
-    int *pend;                                  // n-order tree: pending-cut rings [P][pend_cap][2]
-    int pend_cap;
     int32_t *spikes;                            // segments mode (one job): K per pixel, or nullptr
     int32_t *counts, *seg_ts, *seg_te, *seg_n;  // segments mode: the stable sequences
     float *seg_v;
@@ -497,6 +497,84 @@ __device__ __forceinline__ void carry_store(int *c, int64_t P, int64_t p, const 
     c[19 * P] = npend > 1 ? fs.ri[fs.slot(pj + 1)] : 0;
 }
 
+// Carried state of one pixel of the n-order tree between pieces of a live stream, [rows][P]:
+// the scan's scalars (its pending-cut ring stays in the stream's ring buffer), the frame
+// sink's frames written and last final cut (every released cut is final, so none is pending
+// at a piece end), and every node field.
+constexpr int TREE_ROW_PH = 2, TREE_ROW_NP = 3, TREE_CARRY_FIXED = 11;
+template <class Tree>
+constexpr int tree_carry_rows() { return TREE_CARRY_FIXED + Tree::NF * (Tree::TOPN + Tree::DEEPN); }
+
+template <class Tree, typename OutT>
+__device__ __forceinline__ void tree_carry_load(const int *c, int64_t P, int64_t p, Tree &sc, FrameSink<OutT> &fs) {
+    c += p;
+    sc.last_t = c[0 * P];
+    sc.nint = c[1 * P];
+    sc.ph = c[2 * P];
+    sc.np = c[3 * P];
+    sc.thead = c[4 * P];
+    sc.tlast = c[5 * P];
+    sc.rel_t = c[6 * P];
+    sc.bad = c[7 * P];
+    fs.W = fs.kf = c[8 * P];
+    fs.ct = c[9 * P];
+    fs.ci = c[10 * P];
+    const int *t = c + static_cast<int64_t>(TREE_CARRY_FIXED) * P;
+#pragma unroll
+    for (int f = 0; f < Tree::NF; ++f)
+#pragma unroll
+        for (int k = 0; k < Tree::TOPN; ++k) sc.top[f][k] = t[static_cast<int64_t>(f * Tree::TOPN + k) * P];
+    if constexpr (Tree::NODES > Tree::TOPN) {
+        const int *d = t + static_cast<int64_t>(Tree::NF * Tree::TOPN) * P;
+        for (int k = 0; k < Tree::NF * Tree::DEEPN; ++k) sc.deep[k] = d[static_cast<int64_t>(k) * P];
+    }
+}
+
+template <class Tree, typename OutT>
+__device__ __forceinline__ void tree_carry_store(int *c, int64_t P, int64_t p, const Tree &sc,
+                                                 const FrameSink<OutT> &fs) {
+    c += p;
+    c[0 * P] = sc.last_t;
+    c[1 * P] = sc.nint;
+    c[2 * P] = sc.ph;
+    c[3 * P] = sc.np;
+    c[4 * P] = sc.thead;
+    c[5 * P] = sc.tlast;
+    c[6 * P] = sc.rel_t;
+    c[7 * P] = sc.bad;
+    c[8 * P] = fs.W;
+    c[9 * P] = fs.ct;
+    c[10 * P] = fs.ci;
+    int *t = c + static_cast<int64_t>(TREE_CARRY_FIXED) * P;
+#pragma unroll
+    for (int f = 0; f < Tree::NF; ++f)
+#pragma unroll
+        for (int k = 0; k < Tree::TOPN; ++k) t[static_cast<int64_t>(f * Tree::TOPN + k) * P] = sc.top[f][k];
+    if constexpr (Tree::NODES > Tree::TOPN) {
+        int *d = t + static_cast<int64_t>(Tree::NF * Tree::TOPN) * P;
+        for (int k = 0; k < Tree::NF * Tree::DEEPN; ++k) d[static_cast<int64_t>(k) * P] = sc.deep[k];
+    }
+}
+
+// A live stream's pending-cut rings grown from old_cap to new_cap cuts per pixel: each
+// pixel's np pending cuts, first at slot ph, move to slots 0 .. np-1 of its new ring and
+// its carried ph becomes 0.
+__global__ void tree_ring_grow_kernel(const int *old_ring, int old_cap, int *new_ring, int new_cap, int *carry,
+                                      int64_t P) {
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < P;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int ph = carry[TREE_ROW_PH * P + p], np = carry[TREE_ROW_NP * P + p];
+        const int *o = old_ring + p * 2 * old_cap;
+        int *n = new_ring + p * 2 * new_cap;
+        for (int j = 0; j < np && j < new_cap; ++j) {
+            const int sl = (ph + j) & (old_cap - 1);
+            n[2 * j] = o[2 * sl];
+            n[2 * j + 1] = o[2 * sl + 1];
+        }
+        carry[TREE_ROW_PH * P + p] = 0;
+    }
+}
+
 // ORDER: 1 FSR, 2 SSR, 3 TFI, TREE_ORDER0 + n the n-order tree (n = 3..5 levels)
 constexpr int TREE_ORDER0 = 10;
 // The tree's first levels keep their node state in registers (7 nodes), deeper ones in local
@@ -560,8 +638,8 @@ __global__ void __launch_bounds__(NTHREADS, ORDER > TREE_ORDER0 ? tree_min_block
     Scan sc;
     int tree_deep[TREE ? Tree::NF * Tree::DEEPN : 1];  // the tree's deep levels (local memory)
     if constexpr (TREE) {  // the pixel's ring: pend_cap (t, i) pairs, contiguous
-        int *ring = prm.pend + (job.pend_px + (valid ? p : 0)) * 2 * prm.pend_cap;
-        sc.init(tree_deep, ring, ring + 1, 2, prm.pend_cap);
+        int *ring = job.pend + static_cast<int64_t>(valid ? p : 0) * 2 * job.pend_cap;
+        sc.init(tree_deep, ring, ring + 1, 2, job.pend_cap);
     } else {
         sc.init();
     }
@@ -586,8 +664,11 @@ __global__ void __launch_bounds__(NTHREADS, ORDER > TREE_ORDER0 ? tree_min_block
         fs.cvb = 0;
         fs.zero_tail = (job.edges & EDGE_ZERO_TAIL) != 0;
         fs.cur_o = from_bits<OutT>(0);
-        if constexpr (!TREE)
-            if (!(job.flags & JOB_FIRST) && valid) carry_load(job.carry, job.P, p, sc, fs);
+        if (!(job.flags & JOB_FIRST) && valid) {
+            // (one-job launches of the tree are whole streams: live pieces come in batches)
+            if constexpr (!TREE) carry_load(job.carry, job.P, p, sc, fs);
+            else if constexpr (MAXJ > 1) tree_carry_load(job.carry, job.P, p, sc, fs);
+        }
     }
 
     bool ok = true;
@@ -671,11 +752,17 @@ __global__ void __launch_bounds__(NTHREADS, ORDER > TREE_ORDER0 ? tree_min_block
         // piece end: convert the final cuts and write every resolved frame; the last
         // converted cut starts the open span, the rest are pending candidates
         flush_rows(fs, sc.frontier(), valid, true);
-        if constexpr (!TREE) {
-            if (valid) {
+        if (valid) {
+            if constexpr (!TREE) {
                 const int npend = fs.tail - fs.conv;
                 if (npend > 2 || fs.bad) atomicOr(prm.status, DEV_INTERNAL);
                 carry_store(job.carry, job.P, p, sc, fs, npend > 2 ? 2 : npend, fs.conv);
+            } else if constexpr (MAXJ > 1) {
+                if (fs.tail != fs.conv || fs.bad) atomicOr(prm.status, DEV_INTERNAL);
+                if (sc.bad)
+                    atomicOr(prm.status, (sc.bad & spk::TREE_BAD_ORDER ? DEV_INTERNAL : 0) |
+                                             (sc.bad & spk::TREE_BAD_FULL ? DEV_PEND_FULL : 0));
+                tree_carry_store(job.carry, job.P, p, sc, fs);
             }
         }
     }
@@ -904,8 +991,15 @@ struct spk_stream {
     int H, W, T;
     int64_t pushed;  // steps pushed so far
     int device;
-    int *d_carry;    // [CARRY_INTS][H*W]
+    int order_n;     // n-order tree: levels (0 for the other methods)
+    int *d_carry;    // [CARRY_INTS][H*W], or the tree's [tree rows][H*W]
     int *d_ready;    // min over pixels of frames written, after the last push
+    // n-order tree: the stream's pending-cut rings [H*W][pend_cap][2], and copies of the
+    // carry and the rings taken before each launch (a launch that runs a ring full is rerun
+    // from them with rings twice as large)
+    int *d_pend, *d_carry_bak, *d_pend_bak;
+    int pend_cap;
+    size_t carry_bytes;
 };
 
 // Device allocations of the library go through dev_malloc, which a test hook can make fail
@@ -1192,13 +1286,26 @@ int fill_job(spk_ctx *ctx, CUtensorMap *map, Job *job, const uint8_t *stream, in
     return static_cast<int>((P + BLOCK_PIX - 1) / BLOCK_PIX);
 }
 
-// The n-order tree holds cuts that are not final yet in a per-pixel ring (npix pixels over
-// the launch's jobs, each job's from its pend_px on).  A pixel whose ring runs full reports
-// it; the launch then runs again with rings twice as large, so every valid stream is
-// reconstructed (at most T_max + 1 cuts can be pending; the jobs are whole streams, so a
-// rerun rewrites every output).  Synchronous.
+// The n-order tree holds cuts that are not final yet in a per-pixel ring: for whole streams
+// in the context's rings (npix pixels over the launch's jobs, each job's from its pend_px
+// on), for a piece of a live stream (live[k] != nullptr) in the stream's own rings, which
+// carry pending cuts from piece to piece.  A pixel whose ring runs full reports it; the
+// launch then runs again with rings twice as large: whole streams from scratch, live streams
+// from copies of their carried state and rings taken before the launch (the pending cuts
+// moved into the larger rings), so every valid stream is reconstructed (at most T + 1
+// cuts can be pending).  Synchronous.
 template <int MAXJ>
-int run_norder(spk_ctx *ctx, Batch<MAXJ> &prm, int nblocks, bool segments, int64_t npix, int T_max) {
+int run_norder(spk_ctx *ctx, Batch<MAXJ> &prm, int nblocks, bool segments, int64_t npix, int T_max,
+               spk_stream *const *live = nullptr) {
+    for (int k = 0; live && k < prm.njobs; ++k) {
+        spk_stream *st = live[k];
+        if (!st || (prm.jobs[k].flags & JOB_FIRST)) continue;
+        const size_t ring = static_cast<size_t>(st->H) * st->W * 2 * st->pend_cap * sizeof(int);
+        if (cudaMemcpyAsync(st->d_carry_bak, st->d_carry, st->carry_bytes, cudaMemcpyDeviceToDevice, ctx->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(st->d_pend_bak, st->d_pend, ring, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+            return fail(ctx, SPK_ERR_CUDA, "copy of a live stream's state failed");
+    }
     int pcap = g_norder_cap0.load();
     for (;;) {
         const size_t need = static_cast<size_t>(2) * static_cast<size_t>(pcap) * static_cast<size_t>(npix) * sizeof(int);
@@ -1215,8 +1322,11 @@ int run_norder(spk_ctx *ctx, Batch<MAXJ> &prm, int nblocks, bool segments, int64
             }
             ctx->pend_bytes = need;
         }
-        prm.pend = ctx->d_pend;
-        prm.pend_cap = pcap;
+        for (int k = 0; k < prm.njobs; ++k) {
+            spk_stream *st = live ? live[k] : nullptr;
+            prm.jobs[k].pend = st ? st->d_pend : ctx->d_pend + prm.jobs[k].pend_px * 2 * pcap;
+            prm.jobs[k].pend_cap = st ? st->pend_cap : pcap;
+        }
         int rc = dispatch(ctx, prm, nblocks, segments, TT_DEFAULT);
         if (rc) return rc;
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -1229,6 +1339,44 @@ int run_norder(spk_ctx *ctx, Batch<MAXJ> &prm, int nblocks, bool segments, int64
         if (cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess)
             return fail(ctx, SPK_ERR_CUDA, "status reset failed");
         pcap *= 2;
+        // every live stream of the launch: rings twice as large, filled from the copies, and
+        // the carried state restored
+        for (int k = 0; live && k < prm.njobs; ++k) {
+            spk_stream *ls = live[k];
+            if (!ls) continue;
+            const int64_t P = static_cast<int64_t>(ls->H) * ls->W;
+            const int ncap = 2 * ls->pend_cap;
+            const size_t ring = static_cast<size_t>(P) * 2 * ncap * sizeof(int);
+            int *nr = nullptr, *nb = nullptr;
+            if (dev_malloc(&nr, ring) != cudaSuccess || dev_malloc(&nb, ring) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(nr);
+                return fail(ctx, SPK_ERR_OOM, "cudaMalloc(%zu) of a live stream's pending-cut rings failed", ring);
+            }
+            if (!(prm.jobs[k].flags & JOB_FIRST)) {
+                tree_ring_grow_kernel<<<static_cast<unsigned>(std::min<int64_t>((P + 255) / 256, 4096)), 256, 0,
+                                        ctx->stream>>>(ls->d_pend_bak, ls->pend_cap, nr, ncap, ls->d_carry_bak, P);
+                if (cudaGetLastError() != cudaSuccess ||
+                    cudaMemcpyAsync(ls->d_carry, ls->d_carry_bak, ls->carry_bytes, cudaMemcpyDeviceToDevice,
+                                    ctx->stream) != cudaSuccess ||
+                    cudaMemcpyAsync(nb, nr, ring, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+                    cudaFree(nr);
+                    cudaFree(nb);
+                    return fail(ctx, SPK_ERR_CUDA, "regrowth of a live stream's rings failed");
+                }
+                ++ctx->launches;
+            }
+            if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+                cudaFree(nr);
+                cudaFree(nb);
+                return fail(ctx, SPK_ERR_CUDA, "regrowth of a live stream's rings failed");
+            }
+            cudaFree(ls->d_pend);
+            cudaFree(ls->d_pend_bak);
+            ls->d_pend = nr;
+            ls->d_pend_bak = nb;
+            ls->pend_cap = ncap;
+        }
     }
 }
 
@@ -1252,6 +1400,24 @@ int run_scan(spk_ctx *ctx, const uint8_t *stream, int H, int W, int T, float thr
     prm.cap = cap;
     if (ctx->cfg.method != SPK_NORDER) return dispatch(ctx, prm, nb, segments, tile);
     return run_norder(ctx, prm, nb, segments, static_cast<int64_t>(H) * W, T);
+}
+
+void stream_free(spk_stream *st) {
+    cudaFree(st->d_carry);
+    cudaFree(st->d_ready);
+    cudaFree(st->d_pend);
+    cudaFree(st->d_carry_bak);
+    cudaFree(st->d_pend_bak);
+    delete st;
+}
+
+// rows of carried state per pixel of an n-order tree stream (the kernel's tree type)
+int tree_carry_rows_of(int n) {
+    switch (n) {
+        case 3: return tree_carry_rows<spk::TreeScan<3, 3 < TREE_REG_LEVELS ? 3 : TREE_REG_LEVELS>>();
+        case 4: return tree_carry_rows<spk::TreeScan<4, 4 < TREE_REG_LEVELS ? 4 : TREE_REG_LEVELS>>();
+        default: return tree_carry_rows<spk::TreeScan<5, 5 < TREE_REG_LEVELS ? 5 : TREE_REG_LEVELS>>();
+    }
 }
 
 bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
@@ -1384,8 +1550,7 @@ int spk_stream_open(spk_ctx *ctx, int H, int W, int T, spk_stream **out) {
     ctx->msg[0] = 0;
     if (!out) return fail(ctx, SPK_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (ctx->cfg.method == SPK_TFP || ctx->cfg.method == SPK_NORDER)
-        return fail(ctx, SPK_ERR_ARG, "TFP and the n-order tree run whole streams only");
+    if (ctx->cfg.method == SPK_TFP) return fail(ctx, SPK_ERR_ARG, "TFP runs whole streams only");
     if (H <= 0 || W <= 0 || T <= 0 || T > (1 << 30)) return fail(ctx, SPK_ERR_ARG, "bad H, W or T");
     if (static_cast<int64_t>(H) * W > (1LL << 31) - BLOCK_PIX) return fail(ctx, SPK_ERR_ARG, "H*W too large");
     if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "cudaSetDevice failed");
@@ -1395,17 +1560,24 @@ int spk_stream_open(spk_ctx *ctx, int H, int W, int T, spk_stream **out) {
     st->W = W;
     st->T = T;
     st->device = ctx->cfg.device;
-    const size_t carry_bytes = static_cast<size_t>(CARRY_INTS) * static_cast<size_t>(H) * static_cast<size_t>(W) * 4;
-    if (dev_malloc(&st->d_carry, carry_bytes) != cudaSuccess || dev_malloc(&st->d_ready, sizeof(int)) != cudaSuccess) {
+    const size_t P = static_cast<size_t>(H) * static_cast<size_t>(W);
+    const bool tree = ctx->cfg.method == SPK_NORDER;
+    st->order_n = tree ? ctx->cfg.stability_order : 0;
+    st->carry_bytes = static_cast<size_t>(tree ? tree_carry_rows_of(st->order_n) : CARRY_INTS) * P * 4;
+    st->pend_cap = tree ? g_norder_cap0.load() : 0;
+    const size_t ring_bytes = P * 2 * static_cast<size_t>(st->pend_cap) * sizeof(int);
+    bool ok = dev_malloc(&st->d_carry, st->carry_bytes) == cudaSuccess &&
+              dev_malloc(&st->d_ready, sizeof(int)) == cudaSuccess;
+    if (ok && tree)
+        ok = dev_malloc(&st->d_carry_bak, st->carry_bytes) == cudaSuccess &&
+             dev_malloc(&st->d_pend, ring_bytes) == cudaSuccess && dev_malloc(&st->d_pend_bak, ring_bytes) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
-        if (st->d_carry) cudaFree(st->d_carry);
-        delete st;
+        stream_free(st);
         return fail(ctx, SPK_ERR_OOM, "cudaMalloc of the stream state failed");
     }
     if (cudaMemsetAsync(st->d_ready, 0, sizeof(int), ctx->stream) != cudaSuccess) {
-        cudaFree(st->d_carry);
-        cudaFree(st->d_ready);
-        delete st;
+        stream_free(st);
         return fail(ctx, SPK_ERR_CUDA, "cudaMemsetAsync failed");
     }
     *out = st;
@@ -1418,9 +1590,7 @@ int spk_stream_close(spk_ctx *ctx, spk_stream *s) {
         cudaSetDevice(ctx->cfg.device);
         cudaStreamSynchronize(ctx->stream);
     }
-    cudaFree(s->d_carry);
-    cudaFree(s->d_ready);
-    delete s;
+    stream_free(s);
     return SPK_OK;
 }
 
@@ -1458,8 +1628,9 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
         if (!is_device_ptr(jb.stream) || !is_device_ptr(jb.out_frames))
             return fail(ctx, SPK_ERR_ARG, "job %d: stream and out_frames must be device memory", k);
         if (jb.state) {
-            if (ctx->cfg.method == SPK_TFP || ctx->cfg.method == SPK_NORDER)
-                return fail(ctx, SPK_ERR_ARG, "TFP and the n-order tree run whole streams only");
+            if (ctx->cfg.method == SPK_TFP) return fail(ctx, SPK_ERR_ARG, "TFP runs whole streams only");
+            if (jb.state->order_n != (ctx->cfg.method == SPK_NORDER ? ctx->cfg.stability_order : 0))
+                return fail(ctx, SPK_ERR_ARG, "job %d: stream opened for another method", k);
             if (jb.state->H != jb.H || jb.state->W != jb.W) return fail(ctx, SPK_ERR_ARG, "job %d: H, W differ from its stream", k);
             if (jb.state->pushed + jb.n > jb.state->T) return fail(ctx, SPK_ERR_ARG, "job %d: piece runs past the stream's T", k);
             if (jb.state->device != ctx->cfg.device) return fail(ctx, SPK_ERR_ARG, "job %d: stream on another device", k);
@@ -1491,6 +1662,7 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
         const int nj = njobs - k0 < MAXJ_BATCH ? njobs - k0 : MAXJ_BATCH;
         int blocks = 0, T_max = 0;
         int64_t npix = 0;
+        spk_stream *live[MAXJ_BATCH];
         for (int k = 0; k < nj && rc == SPK_OK; ++k) {
             const spk_job &jb = jobs[order[k0 + k]];
             spk_stream *st = jb.state;
@@ -1509,15 +1681,18 @@ int spk_run(spk_ctx *ctx, const spk_job *jobs, int njobs) {
                 rc = nb;
             } else {
                 blocks += nb;
-                prm->jobs[k].pend_px = npix;  // the n-order tree's rings, job after job
-                npix += static_cast<int64_t>(jb.H) * jb.W;
-                if (jb.n > T_max) T_max = jb.n;
+                live[k] = st;
+                if (!st) {  // the n-order tree's rings of whole streams, job after job
+                    prm->jobs[k].pend_px = npix;
+                    npix += static_cast<int64_t>(jb.H) * jb.W;
+                }
+                if (T > T_max) T_max = T;
             }
         }
         if (rc) break;
         prm->njobs = nj;
         prm->status = ctx->d_status;
-        rc = ctx->cfg.method == SPK_NORDER ? run_norder(ctx, *prm, blocks, false, npix, T_max)
+        rc = ctx->cfg.method == SPK_NORDER ? run_norder(ctx, *prm, blocks, false, npix, T_max, live)
                                            : dispatch(ctx, *prm, blocks, false, tile_of(ctx, false));
         if (rc == SPK_OK)
             for (int k = 0; k < nj; ++k)

@@ -92,13 +92,109 @@ def test_norder_scene_workload(env, n):
     _check(env, st, w.H, w.W, w.T, n, w.stride)
 
 
-def test_norder_runs_whole_streams_only(env):
-    """Live streams are refused (the tree's state is not carried between pieces)."""
+def _push_pieces(pkg, R, S, st, T, rng, sizes=(1, 31, 32, 33, 64, 200, 701)):
+    """Pushes the stream in pieces; returns (frames ready at the end, number of pieces)."""
+    t, last_ready, pieces = 0, 0, 0
+    while t < T:
+        n = int(min(T - t, rng.choice(sizes)))
+        pkg.spk_run(R.ctx, [S.job(torch.from_numpy(np.ascontiguousarray(st[t:t + n])).cuda(), n)])
+        t += n
+        pieces += 1
+        assert S.steps == t
+        ready = S.ready()
+        assert ready >= last_ready
+        last_ready = ready
+    return last_ready, pieces
+
+
+@pytest.mark.parametrize("n,ring0", [(3, 0), (4, 0), (5, 0), (3, 2), (5, 2)])
+def test_norder_live_stream_pieces_equal_whole(env, n, ring0):
+    """A live stream of the tree pushed in pieces of uneven length (node state and pending
+    cuts carried on the device from piece to piece) equals the whole stream bit for bit and
+    the oracle within 1e-6; started with rings of 2 cuts, pieces whose pixels need more run
+    again, from a copy of the state taken before them, with rings twice as large."""
     from paper_2412_11639_gb300 import spk
-    R = env.Reconstructor(order=5, stability_order=3)
+    w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=12, W=70, T=3000)
+    st, _ = spkgen.make_stream(w)
+    bits = spkgen.pack(_deep_streams(3 * 40, 2500, seed=n), 3, 40)
+    spk.spk_debug_norder_capacity(ring0)
+    try:
+        for stream, H, W, T in ((st, w.H, w.W, w.T), (bits, 3, 40, 2500)):
+            R = env.Reconstructor(order=5, stability_order=n, stride=4)
+            whole = R(torch.from_numpy(np.ascontiguousarray(stream)).cuda(), H, W, T).cpu().numpy()
+            S = env.Stream(R, H, W, T)
+            n0 = spk.spk_launch_count(R.ctx)
+            rng = np.random.default_rng(n + 10 * ring0)
+            ready, pieces = _push_pieces(env, R, S, stream, T, rng)
+            launches = spk.spk_launch_count(R.ctx) - n0
+            assert ready == whole.shape[0]
+            assert launches > pieces if ring0 else launches == pieces   # reruns with larger rings
+            got = S.frames.cpu().numpy()
+            R.synchronize()
+            assert np.array_equal(got.view(np.uint32), whole.view(np.uint32))
+            r = oracle.reconstruct(stream, H, W, T, 1.0, n, 4)
+            g = got.reshape(-1, H * W).astype(np.float64)
+            assert np.all(np.abs(g - r.frames) <= REL_TOL * np.abs(r.frames))
+            S.close()
+            R.close()
+    finally:
+        spk.spk_debug_norder_capacity(0)
+
+
+def test_norder_live_streams_and_whole_streams_in_one_launch(env):
+    """Pieces of three live streams and two whole streams share each spk_run launch; every
+    result equals its stream alone."""
+    rng = np.random.default_rng(5)
+    R = env.Reconstructor(order=5, stability_order=3, stride=3)
+    live = []
+    for k in range(3):
+        H, W, T = int(rng.integers(2, 12)), int(rng.integers(5, 60)), int(rng.integers(500, 2500))
+        w = spkgen.WORKLOADS["dynamic_250x400x20000"].resized(H=H, W=W, T=T, seed=70 + k)
+        stream = spkgen.make_stream(w)[0]
+        alone = R(torch.from_numpy(stream).cuda(), H, W, T).cpu().numpy()
+        live.append([stream, env.Stream(R, H, W, T), 0, alone])
+    whole = []
+    while any(x[2] < x[1].T for x in live):
+        jobs = []
+        for x in live:
+            stream, S, t, _ = x
+            if t < S.T:
+                n = int(min(S.T - t, rng.integers(1, 400)))
+                jobs.append(S.job(torch.from_numpy(np.ascontiguousarray(stream[t:t + n])).cuda(), n))
+                x[2] = t + n
+        if len(whole) < 2:
+            H, W, T = 5, 33, 700 + 300 * len(whole)
+            stream = spkgen.pack(_deep_streams(H * W, T, seed=80 + len(whole)), H, W)
+            d = torch.from_numpy(stream).cuda()
+            o = R.alloc_frames(H, W, T)
+            jobs.append((d, H, W, T, 1.0, o, None))
+            whole.append((d, H, W, T, o))
+        env.spk_run(R.ctx, jobs)
+    R.synchronize()
+    for stream, S, t, alone in live:
+        assert np.array_equal(S.frames.cpu().numpy().view(np.uint32), alone.view(np.uint32))
+        S.close()
+    for d, H, W, T, o in whole:
+        assert np.array_equal(o.cpu().numpy().view(np.uint32), R(d, H, W, T).cpu().numpy().view(np.uint32))
+    R.close()
+
+
+def test_live_stream_refusals(env):
+    """TFP has no live streams; a stream opened for one method is refused by another."""
+    from paper_2412_11639_gb300 import spk
+    R = env.Reconstructor(order=4)
     with pytest.raises(spk.SpkError):
         env.Stream(R, 4, 8, 100)
     R.close()
+    Rs = env.Reconstructor(order=2)
+    S = env.Stream(Rs, 4, 8, 100)
+    Rt = env.Reconstructor(order=5, stability_order=3)
+    piece = torch.zeros((10, spkgen.pitch(4, 8)), dtype=torch.uint8, device="cuda")
+    with pytest.raises(spk.SpkError):
+        env.spk_run(Rt.ctx, [S.job(piece, 10)])
+    S.close()
+    Rs.close()
+    Rt.close()
 
 
 @pytest.mark.parametrize("n,ring0", [(3, 0), (4, 0), (5, 0), (3, 2), (5, 2)])
