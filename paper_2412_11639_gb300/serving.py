@@ -76,12 +76,19 @@ class Server:
     """Continuous-batching server over one libspk context."""
 
     def __init__(self, order: int = 2, stride: int = 1, dtype=None, device: int = 0,
-                 mem_budget: int = 8 << 30, max_streams: int = 64, max_piece: int = 4096):
+                 mem_budget: int = 8 << 30, max_streams: int = 64, max_piece: int = 4096,
+                 stability_order: int = 3):
         import torch
         self.torch = torch
-        self.rec = Reconstructor(order=order, stride=stride, dtype=dtype, device=device)
+        self.rec = Reconstructor(order=order, stride=stride, dtype=dtype, device=device,
+                                 stability_order=stability_order)
         self.stride = stride
-        self.esz = 2 if self.rec.dtype == torch.float16 else 4
+        self.esz = {torch.float16: 2, torch.uint8: 1}.get(self.rec.dtype, 4)
+        # device state per pixel of a live stream: the scan's 20 int32, or for the n-order
+        # tree its carried state and pending-cut rings (64 cuts at first), each with a copy
+        n = stability_order
+        self.state_bytes = (20 * 4 if order != 5 else
+                            2 * 4 * (11 + 8 * (7 + max(1, 2 ** n - 8))) + 2 * 2 * 64 * 4)
         self.mem_budget, self.max_streams, self.max_piece = mem_budget, max_streams, max_piece
         self.results = {}        # rid -> frames (device tensor [T_out][H][W])
         self._cancel = set()
@@ -95,7 +102,7 @@ class Server:
     def mem_needed(self, r: Request) -> int:
         P = r.H * r.W
         T_out = (r.T + self.stride - 1) // self.stride
-        return 20 * 4 * P + T_out * P * self.esz + self.max_piece * r.stream.shape[1]
+        return self.state_bytes * P + T_out * P * self.esz + self.max_piece * r.stream.shape[1]
 
     def run(self, requests, clock=time.perf_counter) -> ServeStats:
         torch = self.torch

@@ -9,7 +9,9 @@ import spkgen
 pytestmark = pytest.mark.gpu
 
 
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("order,n", [(2, 3), (5, 3)])
+def test_served_results_equal_alone(order, n):
+    """SSR, and the n-order tree (n = 3) whose live streams carry the tree's state."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -24,14 +26,14 @@ def test_served_results_equal_alone():
         st, _ = spkgen.make_stream(w)
         t += float(rng.exponential(0.004))
         reqs.append(Request(k, st, H, W, arrival=t, rate=2.0e5))
-    srv = Server(order=2, stride=3, max_streams=4, max_piece=256)
+    srv = Server(order=order, stride=3, max_streams=4, max_piece=256, stability_order=n)
     budget = sorted(srv.mem_needed(r) for r in reqs)[-3:]
     srv.mem_budget = sum(budget)                       # at most ~3 streams at once
     stats = srv.run(reqs)
     assert stats.peak_active >= 2                      # streams overlapped on the device
     assert stats.launches > len(reqs)
     assert 0 < stats.p50_ms <= stats.p99_ms <= stats.max_ms
-    R = pkg.Reconstructor(order=2, stride=3)
+    R = pkg.Reconstructor(order=order, stride=3, stability_order=n)
     for r in reqs:
         alone = R(torch.from_numpy(r.stream).cuda(), r.H, r.W, r.T, 1.0)
         R.synchronize()
