@@ -860,6 +860,99 @@ __global__ void __launch_bounds__(NTHREADS, 3) spk_tfp_kernel(const __grid_const
     }
 }
 
+// ------------------------------------------------------------------ TFI kernel ----
+// TFI (Sec. II) of one whole stream: frame k = theta / (s_{j+1} - s_j) for the interval
+// (s_j, s_{j+1}] holding t_k.  Every interval is its own span, so a lane needs no record
+// ring: at each spike t it writes the frames sampled in (previous spike, t] with the
+// interval's value (at the second spike also the head frames, sampled at or before the
+// first spike: the same value, or 0 under SPK_ZERO_HEAD), and at the end the frames after
+// the last spike (the last value, or 0 under SPK_ZERO_TAIL; 0 everywhere with fewer than
+// two spikes).  A frame goes out as soon as its interval closes, one lane's store at a
+// time.  Same TMA pipeline and transpose as the scan.  (Batches and live streams of TFI
+// run in the scan kernel, whose record ring carries the state between pieces.)
+template <typename OutT, int TT>
+__global__ void __launch_bounds__(NTHREADS, 3) spk_tfi_kernel(const __grid_constant__ Batch<1> prm) {
+    constexpr int WPT = TT / 32;
+    extern __shared__ uint8_t smem_raw[];
+    StageSmem<TT> &sm = *reinterpret_cast<StageSmem<TT> *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Job &job = prm.jobs[0];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], NCW * 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int blk = static_cast<int>(blockIdx.x);
+    if (warp == NCW) {  // producer warp: as in the scan kernel
+        if (lane == 0) {
+            const CUtensorMap *map = &prm.maps[0];
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+            int issued = 0;
+            for (int j = 0; j < job.ntiles; ++j) {
+                const int s = j % NS;
+                if (j >= NS && !mbar_wait(&sm.empty[s], ((j / NS) - 1) & 1, prm.status)) break;
+                mbar_arrive_expect_tx(&sm.full[s], TT * ROW_BYTES);
+                tma_load_2d(&sm.stage[s][0][0], map, &sm.full[s], blk * ROW_BYTES, j * TT);
+                issued = j + 1;
+            }
+            for (int j = issued > NS ? issued - NS : 0; j < issued; ++j)
+                if (!mbar_wait(&sm.full[j % NS], (j / NS) & 1, prm.status)) break;
+        }
+        return;
+    }
+    const int64_t p = static_cast<int64_t>(blk) * BLOCK_PIX + warp * 32 + lane;
+    const bool valid = p < job.P;
+    OutT *col = static_cast<OutT *>(job.out) + (valid ? p : 0);
+    const int stride = job.stride;
+    auto frame_of = [&](int t) {  // t / stride, t >= 0
+        return stride == 1 ? t : static_cast<int>(__umulhi(static_cast<uint32_t>(t), job.div_m) >> job.div_s);
+    };
+    const bool zero_head = (job.edges & EDGE_ZERO_HEAD) != 0;
+    int lt = -1;   // last spike
+    int kh = -1;   // last head frame (sampled at or before the first spike)
+    int kw = 0;    // frames < kw are written
+    int vb = 0;    // value bits of the last interval
+    int nsp = 0;   // spikes so far (saturating at 2)
+    for (int j = 0; j < job.ntiles; ++j) {
+        const int s = j % NS;
+        if (!__all_sync(FULL, mbar_wait(&sm.full[s], (j / NS) & 1, prm.status))) return;
+        uint32_t r[WPT];
+#pragma unroll
+        for (int h = 0; h < WPT; ++h) r[h] = lds_u32(&sm.stage[s][lane + 32 * h][warp * 4]);
+        fence_proxy_async_smem();
+        mbar_arrive(&sm.empty[s]);
+#pragma unroll
+        for (int h = 0; h < WPT; ++h) {
+            uint32_t w = warp_transpose32(r[h], lane);
+            if (!valid) w = 0;
+            const int base = job.t_base + j * TT + h * 32;
+            while (w) {
+                const int t = base + __ffs(w) - 1;
+                w &= w - 1;
+                if (nsp == 0) {  // the first spike: the head frames wait for the first interval
+                    kh = frame_of(t);
+                } else {
+                    vb = value_bits<OutT>(job.theta, 1, t - lt);
+                    const int ke = min(frame_of(t), job.T_out - 1);
+                    const OutT v = from_bits<OutT>(vb);
+                    const OutT hv = zero_head ? from_bits<OutT>(0) : v;
+                    for (int k = kw; k <= ke; ++k) col[static_cast<int64_t>(k) * job.P] = k <= kh ? hv : v;
+                    kw = max(kw, ke + 1);
+                }
+                lt = t;
+                nsp = min(nsp + 1, 2);
+            }
+        }
+    }
+    if (!valid) return;
+    // the frames after the last spike: tail hold, 0 under the zero-tail policy or with < 2 spikes
+    const OutT tv = from_bits<OutT>(nsp < 2 || (job.edges & EDGE_ZERO_TAIL) ? 0 : vb);
+    for (int k = kw; k < job.T_out; ++k) col[static_cast<int64_t>(k) * job.P] = tv;
+}
+
 // --------------------------------------------------------- refiner input features ----
 // Input of the learned refiner, bf16 with 16 channels per pixel and frame in two
 // channel-chunk planes, [T_out][H][2][W][8]: channel 0 the plain reconstruction of the frame
@@ -1176,6 +1269,18 @@ int launch_tfp(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
     return SPK_OK;
 }
 
+// TFI of one whole stream (one job)
+template <typename OutT>
+int launch_tfi(spk_ctx *ctx, const Batch<1> &prm, int nblocks) {
+    auto kern = spk_tfi_kernel<OutT, TT_DEFAULT>;
+    constexpr size_t bytes = sizeof(StageSmem<TT_DEFAULT>) + 128;
+    kern<<<static_cast<unsigned>(nblocks), NTHREADS, bytes, ctx->stream>>>(prm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SPK_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    ++ctx->launches;
+    return SPK_OK;
+}
+
 // the n-order tree runs single whole streams only (one job per launch), one kernel per
 // order, so that the tree's node state is indexed by constants and stays in registers.
 // (The n-order calls are synchronous and never captured in a graph.)
@@ -1208,7 +1313,9 @@ template <int MAXJ>
 int dispatch_u8(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks) {
     switch (ctx->cfg.method) {
         case SPK_FSR: return launch<1, uint8_t, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
-        case SPK_TFI: return launch<3, uint8_t, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+        case SPK_TFI:
+            if constexpr (MAXJ == 1) return launch_tfi<uint8_t>(ctx, prm, nblocks);
+            else return launch<3, uint8_t, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
         case SPK_TFP: return launch_tfp<uint8_t, MAXJ>(ctx, prm, nblocks);
         case SPK_NORDER: return launch_norder<uint8_t, false>(ctx, prm, nblocks);
         default: return launch<2, uint8_t, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
@@ -1229,9 +1336,13 @@ int dispatch(spk_ctx *ctx, const Batch<MAXJ> &prm, int nblocks, bool segments, i
                                  : launch<2, float, true, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
     if (m == SPK_NORDER)
         return f16 ? launch_norder<__half, false>(ctx, prm, nblocks) : launch_norder<float, false>(ctx, prm, nblocks);
-    if (m == SPK_TFI)
-        return f16 ? launch<3, __half, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
-                   : launch<3, float, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+    if (m == SPK_TFI) {  // one whole stream: the streaming TFI kernel; batches and pieces: the scan
+        if constexpr (MAXJ == 1)
+            return f16 ? launch_tfi<__half>(ctx, prm, nblocks) : launch_tfi<float>(ctx, prm, nblocks);
+        else
+            return f16 ? launch<3, __half, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks)
+                       : launch<3, float, false, MAXJ, TT_DEFAULT>(ctx, prm, nblocks);
+    }
     if (m == SPK_TFP)
         return f16 ? launch_tfp<__half, MAXJ>(ctx, prm, nblocks) : launch_tfp<float, MAXJ>(ctx, prm, nblocks);
     if (tile == 32) return dispatch_tile<MAXJ, 32>(ctx, prm, nblocks);
