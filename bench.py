@@ -362,6 +362,34 @@ def large_sensor_record(local_rank: int, order: int, steps: int = 3, warmup: int
                          "kernel": KERNEL, "kernel_ms": ms, "algorithmic_bytes_per_launch": alg_bytes}}
 
 
+def host_link(h_in, h_out, units: int, reps: int = 3) -> dict:
+    """This machine's host link, measured with the e2e's own page-locked buffers: plain copies of
+    the step's input to the device and of its frames back (CUDA events, a side stream), and
+    the throughput a step could reach if it were only those copies, overlapped."""
+    import torch
+    s = torch.cuda.Stream()
+    d_in = torch.empty(h_in.numel(), dtype=h_in.dtype, device="cuda")
+    d_out = torch.empty(h_out.numel(), dtype=h_out.dtype, device="cuda")
+    rates = {}
+    with torch.cuda.stream(s):
+        for name, f, nbytes in (("h2d", lambda: d_in.copy_(h_in.view(-1), non_blocking=True),
+                                 h_in.numel() * h_in.element_size()),
+                                ("d2h", lambda: h_out.view(-1).copy_(d_out, non_blocking=True),
+                                 h_out.numel() * h_out.element_size())):
+            f()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            for _ in range(reps):
+                f()
+            b.record(s)
+            s.synchronize()
+            rates[name] = nbytes * reps / (a.elapsed_time(b) / 1e3) / 1e9
+    del d_in, d_out
+    t = max(h_in.numel() * h_in.element_size() / (rates["h2d"] * 1e9),      # seconds per step
+            h_out.numel() * h_out.element_size() / (rates["d2h"] * 1e9))
+    return {"h2d_GBps": rates["h2d"], "d2h_GBps": rates["d2h"], "copy_bound_value": units / t / 1e9, "unit": UNIT}
+
+
 def methods_record(dev, w, local_rank: int, steps: int = 5, warmup: int = 3):
     """The other reconstruction methods on the same resident stream and frame layout (FSR,
     the TFI and TFP baselines, the n-order tree at n = 3, 4, 5), each timed with CUDA events
@@ -471,7 +499,8 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": w.P * w.T_out * args.e2e_steps * world / te_dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(st.nbytes), "d2h_bytes_per_step": int(h_out[0].numel() * esz),
                "api": "spk_reconstruct_host_async x steps, then spk_synchronize",
-               "single_call_ms": one_call * 1e3}
+               "single_call_ms": one_call * 1e3,
+               "link": host_link(h_in, h_out[0], w.P * w.T_out)}
     R.close()
 
     refined = None
