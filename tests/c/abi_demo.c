@@ -2,7 +2,9 @@
  * The C ABI used from plain C (no Python): a stream whose pixel p spikes every (p % 7) + 1
  * steps has constant intervals, so every frame of every pixel is theta / interval (Eq. 4 of
  * one stable sequence).  Reconstructs it through spk_reconstruct_host and the asynchronous
- * variant, checks every frame, and checks the error codes of a few bad calls.
+ * variant, checks every frame, and checks the error codes of a few bad calls.  Then the
+ * same stream as 8-bit frames (theta 255: round(255 / interval), halves up) with both edges
+ * zeroed (frames at or before the first spike and after the last one read 0).
  * Prints "abi_demo ok" and returns 0 on success.
  */
 #include <math.h>
@@ -73,6 +75,33 @@ int main(void) {
     if (spk_reconstruct_host(ctx, stream, H, W, T, 1.0f, frames) != SPK_OK) return 1;
     if (check(frames, T_out, cfg.frame_stride, 1.0f)) return 1;
     spk_destroy(ctx);
+
+    /* 8-bit frames with the zero-head and zero-tail policy */
+    cfg.out_dtype = SPK_U8;
+    cfg.edges = SPK_ZERO_HEAD | SPK_ZERO_TAIL;
+    if (spk_create(&ctx, &cfg) != SPK_OK) {
+        fprintf(stderr, "spk_create (u8): %s\n", spk_last_error(NULL));
+        return 1;
+    }
+    uint8_t *f8 = malloc((size_t)T_out * P);
+    if (spk_reconstruct_host(ctx, stream, H, W, T, 1.5f, f8) != SPK_ERR_ARG) return 1; /* integral theta */
+    if (spk_reconstruct_host(ctx, stream, H, W, T, 255.0f, f8) != SPK_OK) {
+        fprintf(stderr, "spk_reconstruct_host (u8): %s\n", spk_last_error(ctx));
+        return 1;
+    }
+    for (int k = 0; k < T_out; ++k)
+        for (int p = 0; p < P; ++p) {
+            const int d = (p % 7) + 1, t = k * cfg.frame_stride, last = ((T - 1) / d) * d;
+            int want = (2 * 255 + d) / (2 * d);
+            if (want > 255) want = 255;
+            if (t <= 0 || t > last) want = 0;
+            if (f8[(size_t)k * P + p] != want) {
+                fprintf(stderr, "u8 frame %d pixel %d: %d != %d\n", k, p, f8[(size_t)k * P + p], want);
+                return 1;
+            }
+        }
+    spk_destroy(ctx);
+    free(f8);
     free(stream);
     free(frames);
     free(frames2);
