@@ -71,14 +71,16 @@ __host__ __device__ __forceinline__ int64_t act_idx(int n, int y, int x, int c, 
 // [chunk][co][8 channels] (B operand, N = co rows).
 //
 // Persistent and warp-specialised: a block stages the weights once, then walks tasks of
-// RY rows x 128 pixels of one image.  One thread loads halo rows with TMA (512-byte boxes of
+// ry rows x 128 pixels of one image (a task reloads two halo rows, so tall tasks when there
+// are enough of them for every block, 32 rows otherwise).  One thread loads halo rows with TMA (512-byte boxes of
 // the channel-chunk planes) into a ring of
 // RING row slots; one thread issues the MMAs of output row y as soon as rows y - 1 .. y + 1
 // have landed and an accumulator is free, and releases a row slot (tcgen05.commit onto its
 // mbarrier) after the last MMA that reads it; four warps read finished accumulators out of
 // tensor memory and write the output rows.  Loads, MMAs and the write-out of different rows
 // overlap.
-constexpr int RY = 32;  // output rows per task
+constexpr int RY = 32;        // output rows per task, the short form
+constexpr int RY_TALL = 125;  // ... and the tall one (two tasks per column of a 250-row image)
 constexpr long long MMA_WAIT_CYCLES = 4000000000LL;  // ~2 s: bounded waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(192, 4) conv3x3_kernel(const __grid_constant__
                                                       const bf16 *__restrict__ Wt, const float *__restrict__ bias,
                                                       void *Y, const bf16 *__restrict__ mask,
                                                       const float *__restrict__ resid, int N, int H, int W,
-                                                      int *status) {
+                                                      int ry, int *status) {
     using L = ConvSmem<CI, CO>;
     constexpr int CH = L::CH;
     constexpr uint32_t IDESC = mma_idesc(MT, CO);
@@ -257,15 +259,15 @@ __global__ void __launch_bounds__(192, 4) conv3x3_kernel(const __grid_constant__
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int nxs = (W + MT - 1) / MT, nys = (H + RY - 1) / RY;
+    const int nxs = (W + MT - 1) / MT, nys = (H + ry - 1) / ry;
     const int64_t ntask = static_cast<int64_t>(N) * nxs * nys;
     auto geometry = [&](int64_t task, int &n, int &x0, int &y0, int &y1) {
         const int xs = static_cast<int>(task % nxs);
         const int ys = static_cast<int>((task / nxs) % nys);
         n = static_cast<int>(task / (static_cast<int64_t>(nxs) * nys));
         x0 = xs * MT;
-        y0 = ys * RY;
-        y1 = min(H, y0 + RY);
+        y0 = ys * ry;
+        y1 = min(H, y0 + ry);
     };
 
     if (warp == 4) {  // ------------------------------------------------ TMA producer ----
@@ -497,10 +499,14 @@ bool conv(cudaStream_t s, int *status, int N, int H, int W, const bf16 *X, const
     }
     CUtensorMap map, map_tail;
     if (!make_xmap(&map, X, CI, N, H, W, TMA_PX) || !make_xmap(&map_tail, X, CI, N, H, W, TAIL_PX)) return false;
-    const int64_t ntask = static_cast<int64_t>(N) * ((W + MT - 1) / MT) * ((H + RY - 1) / RY);
-    const int64_t grid = std::min<int64_t>(ntask, static_cast<int64_t>(blocks_per_sm) * sms);
+    // tall tasks (fewer halo reloads) when every resident block gets about four of them
+    const int64_t slots = static_cast<int64_t>(blocks_per_sm) * sms;
+    const int nx = (W + MT - 1) / MT;
+    const int ry = static_cast<int64_t>(N) * nx * ((H + RY_TALL - 1) / RY_TALL) >= 4 * slots ? RY_TALL : RY;
+    const int64_t ntask = static_cast<int64_t>(N) * nx * ((H + ry - 1) / ry);
+    const int64_t grid = std::min<int64_t>(ntask, slots);
     conv3x3_kernel<CI, CO, MODE><<<static_cast<unsigned>(grid), 192, bytes, s>>>(map, map_tail, Wt, bias, Y, mask,
-                                                                                  resid, N, H, W, status);
+                                                                                  resid, N, H, W, ry, status);
     return true;
 }
 
