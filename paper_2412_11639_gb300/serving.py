@@ -72,6 +72,17 @@ class ServeStats:
     cancelled: int = 0       # requests cancelled before they finished
 
 
+def stream_state_bytes(order: int, stability_order: int = 3) -> int:
+    """Device bytes per pixel of a live stream's state: the scan's 20 int32, or for the
+    n-order tree (order 5) its carried rows (11 scalars and 8 fields of each of its 7
+    register-level nodes and max(1, 2^n - 8) deeper ones) and its pending-cut rings (64 cuts
+    of two int32 at first), each with the copy taken before a launch."""
+    if order != 5:
+        return 20 * 4
+    n = stability_order
+    return 2 * 4 * (11 + 8 * (7 + max(1, 2 ** n - 8))) + 2 * 2 * 64 * 4
+
+
 class Server:
     """Continuous-batching server over one libspk context."""
 
@@ -84,11 +95,7 @@ class Server:
                                  stability_order=stability_order)
         self.stride = stride
         self.esz = {torch.float16: 2, torch.uint8: 1}.get(self.rec.dtype, 4)
-        # device state per pixel of a live stream: the scan's 20 int32, or for the n-order
-        # tree its carried state and pending-cut rings (64 cuts at first), each with a copy
-        n = stability_order
-        self.state_bytes = (20 * 4 if order != 5 else
-                            2 * 4 * (11 + 8 * (7 + max(1, 2 ** n - 8))) + 2 * 2 * 64 * 4)
+        self.state_bytes = stream_state_bytes(order, stability_order)
         self.mem_budget, self.max_streams, self.max_piece = mem_budget, max_streams, max_piece
         self.results = {}        # rid -> frames (device tensor [T_out][H][W])
         self._cancel = set()

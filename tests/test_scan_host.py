@@ -135,3 +135,25 @@ def test_tree_ring_reports_full_and_large_ring_is_exact(scan_host, tmp_path, ord
     counts, spans = run_host(scan_host, tmp_path, st, w.P, w.T, order, ring=ring)
     assert np.array_equal(counts, ref.nseg)
     assert np.array_equal(spans[:, 1], ref.seg_te)
+
+
+def test_tree_state_sizes_agree(tmp_path):
+    """The n-order tree's per-pixel node state, from the kernel's own type (TreeScan<n, 3> of
+    the scan header, the first three levels in registers), agrees with the carried-state
+    rows the C header documents for live streams (75, 131, 259 int32 for n = 3, 4, 5: 11
+    scalars plus every node field) and with the serving loop's admission estimate."""
+    src = tmp_path / "sizes.cpp"
+    src.write_text('#include <cstdio>\n#include "' + os.path.join(ROOT, "paper_2412_11639_gb300", "csrc",
+                                                               "spk_scan.cuh") + '"\n'
+                   "template <int N> int rows() { using T = spk::TreeScan<N, 3>; return T::NF * (T::TOPN + T::DEEPN); }\n"
+                   'int main() { std::printf("%d %d %d\\n", rows<3>(), rows<4>(), rows<5>()); }\n')
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["g++", "-std=c++17", str(src), "-o", str(exe)])
+    fields = [int(v) for v in subprocess.check_output([str(exe)], text=True).split()]
+    assert [11 + f for f in fields] == [75, 131, 259]
+    header = open(os.path.join(ROOT, "include", "spk.h")).read()
+    assert "75, 131, 259 for" in header
+    from paper_2412_11639_gb300 import serving
+    for n, rows in zip((3, 4, 5), (75, 131, 259)):
+        assert serving.stream_state_bytes(5, n) == 2 * 4 * rows + 2 * 2 * 64 * 4
+    assert serving.stream_state_bytes(2) == 80
